@@ -1,0 +1,181 @@
+/*
+ * dtree.h -- C ABI of the GB300 dual-tree exact k-nearest-neighbour library.
+ *
+ * The library instantiates the dual-tree meta-algorithm of Curtin et al.,
+ * "Tree-Independent Dual-Tree Algorithms" (ICML 2013, Section 2) for exact
+ * k-nearest-neighbour search (Section 5): a kd-tree space tree (Definition 1,
+ * with the kd-tree bounds of Section 3), a pruning dual-tree traversal (the
+ * pruning dual-tree traversal definition of Section 4), the kNN BaseCase
+ * (Algorithm 2) and the kNN Score (Algorithm 3) with the bound B(N_q) of
+ * Section 5.
+ *
+ * Conventions for every entry point:
+ *   - Point arrays are row-major n x d float32.  Pointers marked "device" must
+ *     be CUDA device (or managed) memory on the current device; pointers
+ *     marked "host" are ordinary host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is enqueued on it.
+ *   - Every function returns a dtree_status (0 = success, negative = error);
+ *     no C++ exception crosses the ABI.  On error no output is valid.
+ *   - Handles are not thread-safe: calls that share a handle must not run
+ *     concurrently.
+ */
+#ifndef DTREE_H
+#define DTREE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum dtree_status {
+    DTREE_OK = 0,
+    DTREE_ERR_INVALID_ARG = -1,  /* null pointer, n <= 0, d outside [1, 64], d mismatch,
+                                    leaf_size outside [1, 1024], unknown option value */
+    DTREE_ERR_INVALID_K = -2,    /* k <= 0, or k >= m (bichromatic: the problem statement
+                                    of Section 5 requires 0 < k < m), or k > m - 1
+                                    (monochromatic, the query itself is excluded) */
+    DTREE_ERR_CUDA = -3,         /* a CUDA runtime call or kernel launch failed */
+    DTREE_ERR_OOM = -4,          /* device allocation failed */
+    DTREE_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up (the kernel
+                                    recorded it and returned; the context stays usable) */
+    DTREE_ERR_NOT_TRAINED = -6,  /* a learned proposal was requested without a model */
+    DTREE_ERR_UNSUPPORTED = -7   /* valid request this build/device cannot serve
+                                    (e.g. tensor-core precision on a non-sm_103 device) */
+} dtree_status;
+
+/* Distance arithmetic of the BaseCase tiles.  Whatever the choice, results
+ * are exact: candidates near each query's k-th distance are re-ranked in
+ * float64, and a query whose candidate band overflows is recomputed in
+ * float64 (see dtree_knn). */
+typedef enum dtree_precision {
+    DTREE_PREC_FP32 = 0,   /* CUDA-core float32 differences and squares */
+    DTREE_PREC_TF32 = 1,   /* tensor cores (tcgen05), TF32 inputs, FP32 accumulate */
+    DTREE_PREC_BF16 = 2    /* tensor cores (tcgen05), BF16 inputs, FP32 accumulate */
+} dtree_precision;
+
+/* Options; zero-initialise and set what you need (0 = default). */
+typedef struct dtree_opts {
+    int32_t leaf_size;     /* dtree_build: max points per kd-tree leaf, 1..1024 (default 32) */
+    int32_t precision;     /* dtree_knn: dtree_precision (default FP32) */
+    int32_t query_block;   /* dtree_knn: max queries per work unit (query-tree node), 16..128
+                              (default 128) */
+    int32_t seed_points;   /* dtree_knn: min reference points of the seed subtree evaluated
+                              before the traversal (default 4 * leaf) */
+    int32_t proposal;      /* dtree_knn: 1 = use the attached learned proposal (default 0) */
+    int32_t spin_budget;   /* dtree_knn: iterations of a device-side wait before it gives up
+                              with DTREE_ERR_TIMEOUT (default 1 << 26) */
+    int32_t reserved[10];  /* must be zero */
+} dtree_opts;
+
+/* Counters of one dtree_knn call (all zero if not requested). */
+typedef struct dtree_stats {
+    int64_t node_pairs_scored;   /* Score() evaluations of the traversal */
+    int64_t node_pairs_pruned;   /* pairs whose d_min exceeded B(N_q) */
+    int64_t leaf_pairs_emitted;  /* (query block, reference leaf) pairs that survived */
+    int64_t leaf_pairs_skipped;  /* emitted pairs pruned later by the tightened B */
+    int64_t leaf_pairs_evaluated;/* pairs whose BaseCase tile ran (seed pairs included) */
+    int64_t point_pairs;         /* BaseCase(p_q, p_r) evaluations */
+    int64_t rerank_candidates;   /* candidates re-ranked in float64 */
+    int64_t fallback_blocks;     /* query blocks recomputed in float64 (band overflow) */
+    int64_t query_blocks;        /* work units */
+    int64_t kernel_launches;     /* kernels this call launched */
+    /* device time of each phase in nanoseconds, from CUDA events recorded on
+       `stream` around the phase (only filled when stats are requested) */
+    int64_t ns_seed;             /* seed selection + seed BaseCase */
+    int64_t ns_traverse;         /* bounds + dual-tree traversal + candidate lists */
+    int64_t ns_basecase;         /* main BaseCase pass (tiles, re-rank, output) */
+    int64_t ns_fallback;         /* float64 recomputation of overflowed blocks */
+    int64_t reserved[2];
+} dtree_stats;
+
+typedef struct dtree dtree_t;
+
+/*
+ * dtree_build -- build a kd-tree (a space tree, Definition 1) on the device.
+ *
+ *   pts     device, n x d float32 row-major; read during the call only (the
+ *           tree keeps its own permuted copy, so the caller may free `pts`
+ *           once the call returns).
+ *   n       number of points, 1 <= n < 2^31.
+ *   d       dimension, 1 <= d <= 64.
+ *   opts    nullable; uses leaf_size.
+ *   stream  cudaStream_t or NULL.
+ *   out     receives a library-owned handle; free it with dtree_free.
+ *
+ * The tree is balanced: every split puts floor(n/2) points on the left (the
+ * smallest along the widest dimension of the node's tight bounding box, the
+ * convex set of Definition 1), and all leaves sit at one depth, the smallest
+ * at which every leaf holds at most leaf_size points.  Per node it stores the
+ * box, the box centre (the centroid of Section 3) and an upper bound on the
+ * maximum descendant distance lambda (Section 3).  The call returns after the
+ * tree is complete on `stream`.
+ */
+int dtree_build(const float* pts, int64_t n, int32_t d, const dtree_opts* opts, void* stream,
+                dtree_t** out);
+
+/*
+ * dtree_knn -- exact k nearest neighbours of every point of `query` among the
+ * points of `ref` (problem statement of Section 5).
+ *
+ *   query     tree of the queries, or NULL / the same handle as `ref` for the
+ *             monochromatic case, where a point never returns itself (the
+ *             footnote to Algorithm 2; exclusion is by index, so duplicates at
+ *             distance 0 are valid neighbours).
+ *   ref       tree of the references (m points).
+ *   k         0 < k < m (bichromatic), 0 < k <= m - 1 (monochromatic).
+ *   out_idx   device, n_q x k int64, row i = the query's row in the array it
+ *             was built from; entries are row indices of the reference array,
+ *             ascending by (distance, index) -- ties go to the lower index.
+ *   out_dist  device, n_q x k float32, Euclidean distances (not squared),
+ *             the float64 distance rounded to float32.
+ *   opts      nullable; uses precision, query_block, seed_points, proposal,
+ *             spin_budget.
+ *   stream    cudaStream_t or NULL.
+ *   stats     nullable; receives the call's counters.
+ *
+ * The call enqueues its kernels on `stream`, blocks the calling thread until
+ * they finish (it reads device-side sizes between phases) and returns the
+ * device-side status, so the outputs are ready on return.  Scratch memory
+ * comes from the device's stream-ordered pool.
+ */
+int dtree_knn(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_idx,
+              float* out_dist, const dtree_opts* opts, void* stream, dtree_stats* stats);
+
+/* dtree_free -- release every device allocation of the handle.  NULL-safe.
+ * Must not be called while work that uses the handle is still in flight. */
+void dtree_free(dtree_t* tree);
+
+/* Number of points / dimension / depth (leaves sit at this depth) / leaf
+ * count of a tree; -1 for NULL. */
+int64_t dtree_size(const dtree_t* tree);
+int32_t dtree_dim(const dtree_t* tree);
+int32_t dtree_depth(const dtree_t* tree);
+int64_t dtree_leaf_count(const dtree_t* tree);
+
+/*
+ * dtree_export -- copy the tree's layout to device buffers supplied by the
+ * caller (any of them may be NULL):
+ *   perm    n int32: position in tree order -> row of the build input
+ *   box     nodes x 2 x d float32: lo[0..d) then hi[0..d) per node
+ *   lambda  nodes float32: the stored upper bound on lambda per node
+ *   begin   nodes int32 / count nodes int32: each node's range in tree order
+ * Nodes are numbered in heap order: node i has children 2i+1 and 2i+2,
+ * nodes = 2^(depth+1) - 1.  Enqueued on `stream` and waited for.
+ */
+int dtree_export(const dtree_t* tree, int32_t* perm, float* box, float* lambda, int32_t* begin,
+                 int32_t* count, void* stream);
+
+/* Static description of a status code. */
+const char* dtree_error_string(int status);
+
+/* Kernels launched by this library since the process started (all threads). */
+int64_t dtree_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DTREE_H */

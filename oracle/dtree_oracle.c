@@ -16,7 +16,7 @@
  *
  * Source: Curtin, March, Ram, Anderson, Gray, Isbell, "Tree-Independent
  * Dual-Tree Algorithms", ICML 2013.
- *   - kNN problem statement, Section 4: queries S_q (n x d), references S_r
+ *   - kNN problem statement, Section 5: queries S_q (n x d), references S_r
  *     (m x d), 0 < k < m; N_p / D_p ordered nearest-first; D_p[i] = inf past
  *     the end of the list; in the monochromatic case a point does not return
  *     itself (footnote to Algorithm 2).
@@ -24,7 +24,7 @@
  *     (Section 3 definitions) with the kd-tree bounds given after them.
  *   - DepthFirstTraversal (Algorithm 1), kNN BaseCase (Algorithm 2),
  *     kNN Score (Algorithm 3), the bounds B_1, B_2 and the combined B
- *     (Section 4), Gray's AllNN (Algorithm 4).
+ *     (Section 5), Gray's AllNN (Algorithm 4).
  *
  * Readings of the paper taken here (each one is listed in the design notes):
  *   R1  Euclidean metric; lists compared on squared distance.
@@ -35,7 +35,7 @@
  *   R4  the combined bound is evaluated in its sound form
  *         B(N) = min over N and its ancestors a of min(B_1(a), A(a) + 2 lambda(a)),
  *       A(a) = min over descendant points of D_p[k].  The recursion exactly
- *       as printed in Section 4 is kept as variant BOUND_LITERAL.
+ *       as printed in Section 5 is kept as variant BOUND_LITERAL.
  *   R5  max over an empty set = -inf, min over an empty set = +inf; kd-tree
  *       internal nodes hold no points, leaves hold all of theirs, so
  *       rho(leaf) = lambda(leaf).
@@ -66,7 +66,7 @@
 
 enum {
     BOUND_SOUND = 0,    /* R4 */
-    BOUND_LITERAL = 1,  /* the printed recursion of Section 4, unchanged */
+    BOUND_LITERAL = 1,  /* the printed recursion of Section 5, unchanged */
     BOUND_B1 = 2,       /* B_1 alone (Gray's delta) */
     BOUND_NONE = 3      /* never prune: the plain dual-tree traversal */
 };
@@ -126,7 +126,7 @@ static int list_insert(double* D2, int64_t* N, int k, double d2, int64_t idx) {
 }
 
 /* ---------------------------------------------------------------------- */
-/* brute force: compare every pair, keep the k smallest (Section 4)        */
+/* brute force: compare every pair, keep the k smallest (Section 5)        */
 /* ---------------------------------------------------------------------- */
 
 /* q: nq x d, r: nr x d, row-major float32.  self_idx (nullable): reference

@@ -1,0 +1,435 @@
+// knn_tile.cuh -- the kNN BaseCase (Algorithm 2 of Curtin et al.) on CUDA
+// cores, one CTA per work item of <= 128 queries, one thread per query.
+//
+// For a query block and a list of reference leaves the CTA streams the
+// leaves' points through shared memory and each thread keeps its query's
+// candidate list (distance key, index) sorted in registers: a reference
+// point enters when its key beats the list's last entry, the "d < D[k]"
+// test of Algorithm 2 with ties broken by the lower index.
+//
+// Lists hold KC > k entries.  In float32 the squared distance carries a
+// relative error of at most eps = (DP + 8) 2^-24, so
+//   - an upper bound on the true k-th distance is sqrt(kth * (1 + 2 eps)),
+//     which feeds B_1 and B_2 (Section 5) and the Score test (Algorithm 3)
+//     that skips a leaf whose d_min exceeds the block's bound;
+//   - every true k-nearest neighbour has a float32 key within
+//     band = kth * (1 + 4 eps); at the end those candidates are re-ranked
+//     with the exact float64 distance (the same left-to-right sum as the
+//     definition) and ordered by (distance, reference index).
+// If more than KC - k keys fall inside the band (near-ties or duplicates) the
+// list may have dropped a true neighbour: the block is flagged and
+// recomputed in float64 (MODE_FB), where keys are exact.
+#pragma once
+
+#include "knn_common.cuh"
+
+namespace dt {
+
+template <typename T>
+__device__ __forceinline__ bool key_less(T d, int i, T e, int j) {
+    return d < e || (d == e && i < j);
+}
+
+// Insert (d, i) into the ascending list (bubble through; the last entry falls off).
+template <typename T, int KC>
+__device__ __forceinline__ void list_insert(T (&ld)[KC], int (&li)[KC], T d, int i) {
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+        if (key_less(d, i, ld[j], li[j])) {
+            T td = ld[j];
+            int ti = li[j];
+            ld[j] = d;
+            li[j] = i;
+            d = td;
+            i = ti;
+        }
+    }
+}
+
+template <typename T, int KC>
+__device__ __forceinline__ T list_at(const T (&ld)[KC], int j) {
+    T v = ld[0];
+#pragma unroll
+    for (int q = 1; q < KC; ++q)
+        if (q == j) v = ld[q];
+    return v;
+}
+
+// Exact squared distance: sum over j of (q_j - r_j)^2 in float64, left to
+// right, one rounding per operation (padded dimensions add +0 exactly).
+template <int DP>
+__device__ __forceinline__ double exact_d2(const float* q, const float* r) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < DP; ++j) {
+        double t = __dsub_rn((double)q[j], (double)r[j]);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return s;
+}
+
+template <typename T, int DP>
+__device__ __forceinline__ float ub_of(T kth) {
+    if (sizeof(T) == 8) return __double2float_ru(__dsqrt_ru((double)kth));
+    if (!(kth < INFINITY)) return INFINITY;
+    return __fsqrt_ru(__fmul_ru((float)kth, 1.f + 2.f * rel_eps<DP>()));
+}
+
+template <typename T, int DP, int KC, int MODE>
+__global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
+    constexpr int TN = 4096 / DP;       // staged reference points (16 KB)
+    constexpr int SORTCAP = 2048;       // candidates sorted per window
+    __shared__ __align__(16) float rs[TN * DP];
+    __shared__ int32_t spos[TN];
+    __shared__ int32_t sorig[MODE == MODE_FB ? TN : 1];
+    __shared__ uint64_t scand[MODE == MODE_MAIN ? SORTCAP : 1];
+    __shared__ int3 stab[TN];
+    __shared__ int s_item, s_ntab, s_nst, s_cur, s_part;
+    __shared__ float s_B;
+    __shared__ float s_rmax[kQB / 32], s_rmin[kQB / 32];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nitems = a.nwork * a.cpb;
+    unsigned long long n_skip = 0, n_eval = 0, n_pp = 0, n_re = 0;
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(a.work_ctr, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nitems) break;
+        const int wb = item / a.cpb, chunk = item - wb * a.cpb;
+        const int blk = a.work_blocks ? a.work_blocks[wb] : wb;
+        const int64_t qnode = a.qblock0 + blk;
+        const int nq = min(kQB, a.qcnt[qnode] - chunk * kQB);
+        if (nq > 0) {
+            const bool act = tid < nq;
+            const int myq = a.qbeg[qnode] + chunk * kQB + tid;
+            float q[DP];
+            {
+                const float4* q4 = reinterpret_cast<const float4*>(a.qpts + (int64_t)myq * DP);
+#pragma unroll
+                for (int j = 0; j < DP / 4; ++j) {
+                    float4 v = act ? q4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    q[4 * j] = v.x;
+                    q[4 * j + 1] = v.y;
+                    q[4 * j + 2] = v.z;
+                    q[4 * j + 3] = v.w;
+                }
+            }
+            T ld[KC];
+            int li[KC];
+#pragma unroll
+            for (int j = 0; j < KC; ++j) {
+                ld[j] = (T)INFINITY;
+                li[j] = kEmptyIdx;
+                if (MODE == MODE_MAIN && act) {
+                    ld[j] = (T)a.cand_d[(int64_t)j * a.nq + myq];
+                    li[j] = a.cand_i[(int64_t)j * a.nq + myq];
+                }
+            }
+            const float lam2 = 2.f * a.qlam[qnode];
+            const float Bq = a.Bq ? a.Bq[blk] : INFINITY;
+
+            // the block's live bound: min(B from the traversal, B_1, B_2)
+            auto refresh_bound = [&]() {
+                float ub = ub_of<T, DP>(list_at(ld, a.k - 1));
+                float vmax = act ? ub : -INFINITY, vmin = act ? ub : INFINITY;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
+                    vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, off));
+                }
+                if (lane == 0) {
+                    s_rmax[warp] = vmax;
+                    s_rmin[warp] = vmin;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    for (int w = 1; w < kQB / 32; ++w) {
+                        vmax = fmaxf(vmax, s_rmax[w]);
+                        vmin = fminf(vmin, s_rmin[w]);
+                    }
+                    float b2 = __fadd_ru(vmin, lam2);
+                    s_B = fminf(Bq, fminf(vmax, b2));
+                }
+                __syncthreads();
+            };
+            refresh_bound();
+
+            const int nseed = MODE == MODE_MAIN ? 0 : a.seed_nleaf[blk];
+            const int sleaf0 = MODE == MODE_MAIN ? 0 : a.seed_leaf0[blk];
+            const int64_t c0 = MODE == MODE_SEED ? 0 : a.csr_off[blk];
+            const int64_t c1 = MODE == MODE_SEED ? 0 : a.csr_off[blk + 1];
+            const int64_t ntot = nseed + (c1 - c0);
+            const int64_t win = MODE == MODE_MAIN ? SORTCAP : (ntot > 0 ? ntot : 1);
+
+            for (int64_t w0 = 0; w0 < ntot; w0 += win) {
+                const int wn = (int)(ntot - w0 < win ? ntot - w0 : win);
+                if (MODE == MODE_MAIN) {
+                    int np2 = 1;
+                    while (np2 < wn) np2 <<= 1;
+                    for (int i = tid; i < np2; i += kQB) {
+                        uint64_t key = ~0ull;
+                        if (i < wn) {
+                            int64_t ci = c0 + w0 + i;
+                            key = ((uint64_t)f2o(a.csr_dmin[ci]) << 32) | (uint32_t)a.csr_leaf[ci];
+                        }
+                        scand[i] = key;
+                    }
+                    __syncthreads();
+                    for (int kk = 2; kk <= np2; kk <<= 1)
+                        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                            for (int t = tid; t < np2 / 2; t += kQB) {
+                                int i = 2 * t - (t & (jj - 1));
+                                int l = i + jj;
+                                bool up = (i & kk) == 0;
+                                uint64_t x = scand[i], y = scand[l];
+                                if ((x > y) == up) {
+                                    scand[i] = y;
+                                    scand[l] = x;
+                                }
+                            }
+                            __syncthreads();
+                        }
+                }
+                if (tid == 0) {
+                    s_cur = 0;
+                    s_part = 0;
+                }
+                __syncthreads();
+                while (s_cur < wn) {
+                    // ---- warp 0 fills the stage with whole or partial leaves
+                    if (warp == 0) {
+                        int cur = s_cur, part = s_part, nst = 0, ntab = 0;
+                        const float Bc = s_B;
+                        while (cur < wn && nst < TN) {
+                            int c = cur + lane;
+                            bool valid = c < wn;
+                            int leaf = 0;
+                            float dmin = 0.f;
+                            if (valid) {
+                                if (MODE == MODE_MAIN) {
+                                    uint64_t key = scand[c];
+                                    leaf = (int)(uint32_t)key;
+                                    dmin = o2f((uint32_t)(key >> 32));
+                                } else {
+                                    int64_t ci = w0 + c;
+                                    if (ci < nseed) {
+                                        leaf = sleaf0 + (int)ci;
+                                    } else {
+                                        leaf = a.csr_leaf[c0 + ci - nseed];
+                                        dmin = a.csr_dmin[c0 + ci - nseed];
+                                    }
+                                }
+                            }
+                            bool keep = valid && !(dmin > Bc);
+                            int lb = 0, lc = 0;
+                            if (keep) {
+                                int64_t ln = a.rleaf0 + leaf;
+                                lb = a.rbeg[ln];
+                                lc = a.rcnt[ln];
+                            }
+                            if (lane == 0 && part > 0 && keep) {  // rest of a split leaf
+                                lb += part;
+                                lc -= part;
+                            }
+                            int incl = lc;
+#pragma unroll
+                            for (int off = 1; off < 32; off <<= 1) {
+                                int v = __shfl_up_sync(0xffffffffu, incl, off);
+                                if (lane >= off) incl += v;
+                            }
+                            int excl = incl - lc;
+                            int take = min(max(TN - nst - excl, 0), lc);
+                            bool full = valid && take == lc;
+                            unsigned fm = __ballot_sync(0xffffffffu, full);
+                            int nlead = fm == 0xffffffffu ? 32 : __ffs(~fm) - 1;
+                            bool put = take > 0 && lane <= nlead;
+                            unsigned tm = __ballot_sync(0xffffffffu, put);
+                            if (put) stab[ntab + __popc(tm & ((1u << lane) - 1u))] = make_int3(lb, take, nst + excl);
+                            unsigned sk = __ballot_sync(0xffffffffu, valid && !keep && lane < nlead);
+                            unsigned ev = __ballot_sync(0xffffffffu, keep && lane < nlead);
+                            if (lane == 0) {
+                                n_skip += __popc(sk);
+                                n_eval += __popc(ev);
+                            }
+                            int taken = put ? take : 0;
+#pragma unroll
+                            for (int off = 16; off > 0; off >>= 1) taken += __shfl_xor_sync(0xffffffffu, taken, off);
+                            int pn = __shfl_sync(0xffffffffu, take, nlead & 31);
+                            nst += taken;
+                            ntab += __popc(tm);
+                            if (nlead < 32) {
+                                part = (nlead == 0 ? part : 0) + pn;
+                                cur += nlead;
+                                if (!(cur < wn)) part = 0;
+                                break;  // stage full, or the window is exhausted
+                            }
+                            cur += 32;
+                            part = 0;
+                        }
+                        if (lane == 0) {
+                            s_cur = cur;
+                            s_part = part;
+                            s_nst = nst;
+                            s_ntab = ntab;
+                        }
+                    }
+                    __syncthreads();
+                    // ---- all warps copy the staged rows
+                    const int ntab = s_ntab, nst = s_nst;
+                    for (int t = warp; t < ntab; t += kQB / 32) {
+                        int3 e = stab[t];
+                        const float4* src = reinterpret_cast<const float4*>(a.rpts) + (int64_t)e.x * (DP / 4);
+                        float4* dst = reinterpret_cast<float4*>(rs) + e.z * (DP / 4);
+                        for (int f = lane; f < e.y * (DP / 4); f += 32) dst[f] = src[f];
+                        for (int i = lane; i < e.y; i += 32) {
+                            spos[e.z + i] = e.x + i;
+                            if (MODE == MODE_FB) sorig[e.z + i] = a.ridx[e.x + i];
+                        }
+                    }
+                    __syncthreads();
+                    // ---- BaseCase over the stage
+                    if (act) {
+#pragma unroll 2
+                        for (int e = 0; e < nst; ++e) {
+                            const float4* r4 = reinterpret_cast<const float4*>(rs + e * DP);
+                            T acc = 0;
+#pragma unroll
+                            for (int j = 0; j < DP / 4; ++j) {
+                                float4 v = r4[j];
+                                if (sizeof(T) == 4) {
+                                    float t0 = q[4 * j] - v.x, t1 = q[4 * j + 1] - v.y;
+                                    float t2 = q[4 * j + 2] - v.z, t3 = q[4 * j + 3] - v.w;
+                                    float f = (float)acc;
+                                    f = fmaf(t0, t0, f);
+                                    f = fmaf(t1, t1, f);
+                                    f = fmaf(t2, t2, f);
+                                    f = fmaf(t3, t3, f);
+                                    acc = (T)f;
+                                } else {
+                                    double s = (double)acc;
+                                    const float rv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                                    for (int u = 0; u < 4; ++u) {
+                                        double t = __dsub_rn((double)q[4 * j + u], (double)rv[u]);
+                                        s = __dadd_rn(s, __dmul_rn(t, t));
+                                    }
+                                    acc = (T)s;
+                                }
+                            }
+                            const int rp = spos[e];
+                            const int tie = MODE == MODE_FB ? sorig[e] : rp;
+                            if (key_less(acc, tie, ld[KC - 1], li[KC - 1]) && !(a.mono && rp == myq))
+                                list_insert(ld, li, acc, tie);
+                        }
+                    }
+                    if (tid == 0) n_pp += (unsigned long long)nst * nq;
+                    refresh_bound();
+                }
+                __syncthreads();
+            }
+
+            // ---- finish the work item
+            if (MODE == MODE_SEED) {
+                if (act) {
+#pragma unroll
+                    for (int j = 0; j < KC; ++j) {
+                        a.cand_d[(int64_t)j * a.nq + myq] = (float)ld[j];
+                        a.cand_i[(int64_t)j * a.nq + myq] = li[j];
+                    }
+                }
+            } else if (MODE == MODE_FB) {
+                if (act) {
+                    int64_t base = (int64_t)a.qidx[myq] * a.k;
+#pragma unroll
+                    for (int j = 0; j < KC; ++j)
+                        if (j < a.k) {
+                            a.out_idx[base + j] = li[j];
+                            a.out_dist[base + j] = (float)sqrt((double)ld[j]);
+                        }
+                }
+            } else {
+                const float kth = (float)list_at(ld, a.k - 1);
+                const float band = __fmul_ru(kth, 1.f + 4.f * rel_eps<DP>());
+                const bool ovf = act && li[KC - 1] != kEmptyIdx && !((float)ld[KC - 1] > band);
+                if (__syncthreads_or(ovf)) {
+                    if (tid == 0 && atomicExch(&a.fb_flag[blk], 1) == 0)
+                        a.fb_list[atomicAdd(a.fb_count, 1)] = blk;
+                } else if (act) {
+                    double rd[KC];
+                    int ri[KC];
+#pragma unroll
+                    for (int j = 0; j < KC; ++j) {
+                        rd[j] = (double)INFINITY;
+                        ri[j] = kEmptyIdx;
+                    }
+#pragma unroll
+                    for (int j = 0; j < KC; ++j) {
+                        if (li[j] != kEmptyIdx && !((float)ld[j] > band)) {
+                            float r[DP];
+                            const float4* r4 = reinterpret_cast<const float4*>(a.rpts + (int64_t)li[j] * DP);
+#pragma unroll
+                            for (int u = 0; u < DP / 4; ++u) {
+                                float4 v = r4[u];
+                                r[4 * u] = v.x;
+                                r[4 * u + 1] = v.y;
+                                r[4 * u + 2] = v.z;
+                                r[4 * u + 3] = v.w;
+                            }
+                            list_insert(rd, ri, exact_d2<DP>(q, r), a.ridx[li[j]]);
+                            ++n_re;
+                        }
+                    }
+                    int64_t base = (int64_t)a.qidx[myq] * a.k;
+#pragma unroll
+                    for (int j = 0; j < KC; ++j)
+                        if (j < a.k) {
+                            a.out_idx[base + j] = ri[j];
+                            a.out_dist[base + j] = (float)sqrt(rd[j]);
+                        }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // counters: one atomic per thread that holds any
+    if (n_skip) atomicAdd(&a.stats[ST_SKIPPED], n_skip);
+    if (n_eval) atomicAdd(&a.stats[ST_EVALUATED], n_eval);
+    if (n_pp) atomicAdd(&a.stats[ST_POINT_PAIRS], n_pp);
+    if (n_re) atomicAdd(&a.stats[ST_RERANK], n_re);
+}
+
+template <class K>
+inline int tile_grid(K kern, int items) {
+    int g = occupancy_grid((const void*)kern, kQB, 0);
+    return items < g ? (items > 0 ? items : 1) : g;
+}
+
+template <int DP>
+int launch_tile_cc(const TileArgs& a, int kc, int mode, int items, cudaStream_t s) {
+#define DT_TILE_CASE(KCV)                                                                 \
+    case KCV:                                                                             \
+        if (mode == MODE_SEED) {                                                          \
+            auto kern = k_tile<float, DP, KCV, MODE_SEED>;                                \
+            DT_LAUNCH(kern, tile_grid(kern, items), kQB, 0, s, a);                        \
+        } else if (mode == MODE_MAIN) {                                                   \
+            auto kern = k_tile<float, DP, KCV, MODE_MAIN>;                                \
+            DT_LAUNCH(kern, tile_grid(kern, items), kQB, 0, s, a);                        \
+        } else {                                                                          \
+            auto kern = k_tile<double, DP, KCV, MODE_FB>;                                 \
+            DT_LAUNCH(kern, tile_grid(kern, items), kQB, 0, s, a);                        \
+        }                                                                                 \
+        return DTREE_OK;
+    switch (kc) {
+        DT_TILE_CASE(4)
+        DT_TILE_CASE(8)
+        DT_TILE_CASE(16)
+        DT_TILE_CASE(32)
+        default:
+            return DTREE_ERR_UNSUPPORTED;
+    }
+#undef DT_TILE_CASE
+}
+
+}  // namespace dt

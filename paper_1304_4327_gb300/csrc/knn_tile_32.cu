@@ -1,0 +1,6 @@
+// knn_tile_32.cu -- CUDA-core BaseCase tiles for dimension bucket DP = 32.
+#include "knn_tile.cuh"
+
+namespace dt {
+template int launch_tile_cc<32>(const TileArgs&, int, int, int, cudaStream_t);
+}  // namespace dt

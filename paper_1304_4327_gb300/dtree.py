@@ -1,0 +1,219 @@
+"""Python binding of the C ABI declared in include/dtree.h.
+
+Argument marshalling only: every step of the search runs in the CUDA library
+(``libdtree.so``).  PyTorch supplies device memory and the current stream.
+Importing this module loads the library and fails loudly if it is missing;
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdtree.so")
+
+DTREE_OK = 0
+PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2}
+_I32, _I64, _P = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+
+
+class dtree_opts(ctypes.Structure):
+    _fields_ = [("leaf_size", _I32), ("precision", _I32), ("query_block", _I32),
+                ("seed_points", _I32), ("proposal", _I32), ("spin_budget", _I32),
+                ("reserved", _I32 * 10)]
+
+
+STAT_FIELDS = ("node_pairs_scored", "node_pairs_pruned", "leaf_pairs_emitted",
+               "leaf_pairs_skipped", "leaf_pairs_evaluated", "point_pairs",
+               "rerank_candidates", "fallback_blocks", "query_blocks", "kernel_launches",
+               "ns_seed", "ns_traverse", "ns_basecase", "ns_fallback")
+
+
+class dtree_stats(ctypes.Structure):
+    _fields_ = [(f, _I64) for f in STAT_FIELDS] + [("reserved", _I64 * 2)]
+
+
+class DTreeError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {error_string(status)} ({status})")
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with paper_1304_4327_gb300.build.build() "
+            "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    lib.dtree_build.argtypes = [_P, _I64, _I32, ctypes.POINTER(dtree_opts), _P, ctypes.POINTER(_P)]
+    lib.dtree_knn.argtypes = [_P, _P, _I32, _P, _P, ctypes.POINTER(dtree_opts), _P,
+                              ctypes.POINTER(dtree_stats)]
+    lib.dtree_free.argtypes = [_P]
+    lib.dtree_free.restype = None
+    lib.dtree_size.argtypes = [_P]
+    lib.dtree_size.restype = _I64
+    lib.dtree_dim.argtypes = [_P]
+    lib.dtree_dim.restype = _I32
+    lib.dtree_depth.argtypes = [_P]
+    lib.dtree_depth.restype = _I32
+    lib.dtree_leaf_count.argtypes = [_P]
+    lib.dtree_leaf_count.restype = _I64
+    lib.dtree_export.argtypes = [_P, _P, _P, _P, _P, _P, _P]
+    lib.dtree_error_string.argtypes = [ctypes.c_int]
+    lib.dtree_error_string.restype = ctypes.c_char_p
+    lib.dtree_launch_count.argtypes = []
+    lib.dtree_launch_count.restype = _I64
+    for f in (lib.dtree_build, lib.dtree_knn, lib.dtree_export):
+        f.restype = ctypes.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def error_string(status: int) -> str:
+    return _lib.dtree_error_string(int(status)).decode()
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(_lib.dtree_launch_count())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _opts(**kw) -> dtree_opts:
+    o = dtree_opts()
+    for key, val in kw.items():
+        if val is not None:
+            setattr(o, key, int(val))
+    return o
+
+
+def _check_points(x: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype != torch.float32 or x.dim() != 2:
+        raise TypeError(f"{name} must be a 2-D float32 tensor")
+    return x.contiguous()
+
+
+class Tree:
+    """Owning wrapper of a dtree_t* handle."""
+
+    def __init__(self, handle: int):
+        self.handle = ctypes.c_void_p(handle)
+
+    @property
+    def n(self) -> int:
+        return int(_lib.dtree_size(self.handle))
+
+    @property
+    def d(self) -> int:
+        return int(_lib.dtree_dim(self.handle))
+
+    @property
+    def depth(self) -> int:
+        return int(_lib.dtree_depth(self.handle))
+
+    @property
+    def leaves(self) -> int:
+        return int(_lib.dtree_leaf_count(self.handle))
+
+    def free(self) -> None:
+        if self.handle and self.handle.value:
+            _lib.dtree_free(self.handle)
+            self.handle = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def dtree_build(points: torch.Tensor, leaf_size: int = 32, stream=None) -> Tree:
+    """Build a kd-tree on the device (see dtree_build in include/dtree.h)."""
+    pts = _check_points(points, "points")
+    out = ctypes.c_void_p()
+    o = _opts(leaf_size=leaf_size)
+    rc = _lib.dtree_build(ctypes.c_void_p(pts.data_ptr()), pts.shape[0], pts.shape[1],
+                          ctypes.byref(o), _stream(stream), ctypes.byref(out))
+    if rc != DTREE_OK:
+        raise DTreeError(rc, "dtree_build")
+    return Tree(out.value)
+
+
+def dtree_knn(query: Optional[Tree], ref: Tree, k: int, precision: str = "fp32",
+              query_block: int = 0, seed_points: int = 0, out_idx: Optional[torch.Tensor] = None,
+              out_dist: Optional[torch.Tensor] = None, stream=None, with_stats: bool = False):
+    """Exact kNN of every point of ``query`` (None = monochromatic) in ``ref``.
+
+    Returns (idx int64 (n_q, k), dist float32 (n_q, k)) on the device, plus a
+    dict of counters when ``with_stats``.
+    """
+    nq = ref.n if query is None else query.n
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if k <= 0:  # let the library report the invalid k
+        rc = _lib.dtree_knn(None if query is None else query.handle, ref.handle, int(k), None,
+                            None, None, _stream(stream), None)
+        raise DTreeError(rc, "dtree_knn")
+    if out_idx is None:
+        out_idx = torch.empty((nq, k), dtype=torch.int64, device=dev)
+    if out_dist is None:
+        out_dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    if out_idx.shape != (nq, k) or out_idx.dtype != torch.int64 or not out_idx.is_contiguous():
+        raise ValueError("out_idx must be a contiguous int64 (n_q, k) tensor")
+    if out_dist.shape != (nq, k) or out_dist.dtype != torch.float32 or not out_dist.is_contiguous():
+        raise ValueError("out_dist must be a contiguous float32 (n_q, k) tensor")
+    o = _opts(precision=PRECISIONS[precision], query_block=query_block, seed_points=seed_points)
+    st = dtree_stats()
+    rc = _lib.dtree_knn(None if query is None else query.handle, ref.handle, int(k),
+                        ctypes.c_void_p(out_idx.data_ptr()), ctypes.c_void_p(out_dist.data_ptr()),
+                        ctypes.byref(o), _stream(stream), ctypes.byref(st) if with_stats else None)
+    if rc != DTREE_OK:
+        raise DTreeError(rc, "dtree_knn")
+    if with_stats:
+        return out_idx, out_dist, {f: int(getattr(st, f)) for f in STAT_FIELDS}
+    return out_idx, out_dist
+
+
+def dtree_free(tree: Tree) -> None:
+    tree.free()
+
+
+def dtree_export(tree: Tree, stream=None) -> dict:
+    """The tree's layout as device tensors (perm, box, lambda, begin, count)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    nodes = 2 * tree.leaves - 1
+    perm = torch.empty(tree.n, dtype=torch.int32, device=dev)
+    box = torch.empty((nodes, 2, tree.d), dtype=torch.float32, device=dev)
+    lam = torch.empty(nodes, dtype=torch.float32, device=dev)
+    beg = torch.empty(nodes, dtype=torch.int32, device=dev)
+    cnt = torch.empty(nodes, dtype=torch.int32, device=dev)
+    rc = _lib.dtree_export(tree.handle, *(ctypes.c_void_p(t.data_ptr()) for t in (perm, box, lam, beg, cnt)),
+                           _stream(stream))
+    if rc != DTREE_OK:
+        raise DTreeError(rc, "dtree_export")
+    return {"perm": perm, "box": box, "lambda": lam, "begin": beg, "count": cnt}
+
+
+def knn(ref_points: torch.Tensor, query_points: Optional[torch.Tensor], k: int,
+        leaf_size: int = 32, **kw) -> Tuple[torch.Tensor, torch.Tensor]:
+    """Build the tree(s), search, free: the one-call form of the API."""
+    tr = dtree_build(ref_points, leaf_size)
+    tq = None if query_points is None else dtree_build(query_points, leaf_size)
+    try:
+        return dtree_knn(tq, tr, k, **kw)
+    finally:
+        tr.free()
+        if tq is not None:
+            tq.free()

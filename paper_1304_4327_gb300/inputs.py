@@ -63,6 +63,11 @@ def _streams(workload_id: int, n: int = 3):
     return [np.random.Generator(np.random.PCG64(c)) for c in ss.spawn(n)]
 
 
+def _query_stream(workload_id: int, shard: int):
+    """Query stream of one shard (shard 0 is the workload's own query stream)."""
+    return _streams(workload_id, 3 + shard)[2 + shard]
+
+
 def uniform(n: int, d: int, seed: int) -> np.ndarray:
     """n points U[0,1]^d as float32 from one seed (used by tests)."""
     g = np.random.Generator(np.random.PCG64(seed))
@@ -116,8 +121,10 @@ def _gmm(g, centres, n, sigma):
 
 
 def gmm16(n_ref: int = 4_000_000, n_query: int = 1_000_000, d: int = 16, k: int = 10,
-          n_comp: int = 32, leaf_size: int = 32) -> Workload:
-    gp, gr, gq = _streams(2)
+          n_comp: int = 32, leaf_size: int = 32, shard: int = 0) -> Workload:
+    """``shard`` > 0 draws an independent query set (one per GPU of a weak-scaling run)."""
+    gp, gr, _ = _streams(2)
+    gq = _query_stream(2, shard)
     centres = gp.uniform(-10.0, 10.0, size=(n_comp, d)).astype(np.float32)
     ref = _gmm(gr, centres, n_ref, 1.0)
     query = _gmm(gq, centres, n_query, 1.0)

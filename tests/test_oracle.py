@@ -209,7 +209,7 @@ def test_parallel_subtrees_equal_serial(par_depth):
 
 
 def test_literal_combined_bound_is_unsound():
-    # The combined recursion exactly as printed in Section 4 uses
+    # The combined recursion exactly as printed in Section 5 uses
     # B(N_c) + 2(lambda_q - lambda_c) for every child, although that step was
     # derived for B_2 only.  On this 6-point input it prunes a true neighbour.
     X = inputs.uniform(6, 2, 13)
