@@ -171,6 +171,74 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# roofline of the BaseCase tile kernel
+# ---------------------------------------------------------------------------
+
+# DRAM bytes (read + write) of one tile-kernel launch pair (seed + main) per
+# evaluated point pair, from an ncu capture of the 400,000 x 100,000 case of
+# the same workload, scaled to a full launch by the point pairs it evaluates.
+# None until a capture of the current kernel exists.
+TRAFFIC_PER_PAIR = {"fp32": None, "tf32": None, "bf16": None}
+
+
+def roofline(precision, d, pairs, ns_tile, sms):
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+        src = "of measured"
+    except (OSError, ValueError):
+        src = "of fallback"
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    secs = ns_tile * 1e-9
+    tpp = TRAFFIC_PER_PAIR.get(precision)
+    traffic = tpp * pairs if tpp is not None else None
+    if precision == "fp32":
+        flops = 3.0 * d * pairs                  # d subtractions + d FMAs (2 flops each)
+        peak = 2.0 * 128 * sms * sm_max * 1e6 / 1e12
+        bound, kernel = "alu", "k_tile (BaseCase, CUDA-core float32)"
+        psrc = f"2 x 128 FP32 lanes x {sms} SMs x {sm_max:.0f} MHz"
+    else:
+        flops = 2.0 * d * pairs                  # one multiply-add per coordinate and pair
+        bf16 = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        peak = bf16 if precision == "bf16" else bf16 * 1.1 / 2.25
+        bound, kernel = "tensor", f"k_tile_tc (BaseCase, tcgen05 {precision})"
+        psrc = (f"measured sustained BF16 dense {bf16:.1f} TFLOP/s ({src})"
+                + ("" if precision == "bf16" else " x 1.1/2.25 (nominal TF32:BF16)"))
+    achieved = flops / secs / 1e12 if secs > 0 else 0.0
+    return {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": traffic,
+            "peak_source": psrc, "algorithmic_flops_per_step": flops,
+            "point_pairs_per_step": pairs, "kernel_ms": ns_tile / 1e6}
+
+
+# ---------------------------------------------------------------------------
+# multi-process helpers (query shards; the slowest rank sets the time)
+# ---------------------------------------------------------------------------
+
+def shard_workload(args, rank):
+    """Rank r searches its own query shard (an independent seeded stream)
+    against the same reference set: the problem splits by queries with no
+    exchange step."""
+    return inputs.gmm16(n_ref=args.n_ref, n_query=args.n_query, leaf_size=args.leaf, shard=rank)
+
+
+def max_over_ranks(x, world, device):
+    """The maximum of a per-rank float over all ranks (identity at world 1)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, n_per_rank, ms_max):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * n_per_rank / (ms_max / 1e3)
+
+
+# ---------------------------------------------------------------------------
 # the CUDA path
 # ---------------------------------------------------------------------------
 
@@ -188,7 +256,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1304_4327_gb300 import dtree
 
-    W = inputs.gmm16(n_ref=args.n_ref, n_query=args.n_query, leaf_size=args.leaf, shard=rank)
+    W = shard_workload(args, rank)
     d, k = W.d, W.k
     ref_d = torch.from_numpy(W.ref).cuda()
     q_d = torch.from_numpy(W.query).cuda()
@@ -232,12 +300,8 @@ def main():
     barrier()
     clock_info = clocks.stop()
     launches = dtree.launch_count() - launches0
-    ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * nq / (ms_max / 1e3)
+    ms_max = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
+    value = job_rate(world, nq, ms_max)
 
     # end to end through the public API: pinned host inputs in, host results out
     ref_h = torch.from_numpy(W.ref).pin_memory()
@@ -257,25 +321,17 @@ def main():
         dist_h.copy_(out_dist, non_blocking=True)
     f1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = torch.tensor([f0.elapsed_time(f1) / args.e2e_steps], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
-    e2e_value = world * nq / (float(e2e_ms.item()) / 1e3)
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1) / args.e2e_steps, world, "cuda")
+    e2e_value = job_rate(world, nq, e2e_ms)
 
-    # roofline of the dominant kernel (the BaseCase tile kernel, CUDA cores)
-    ns_tile = sum(s["ns_seed"] + s["ns_basecase"] + s["ns_fallback"] for s in stats) / len(stats)
+    # roofline of the dominant kernel: the BaseCase tile kernel (its seed and
+    # main launches), timed per call with CUDA events on the launching stream
+    ns_tile = sum(s["ns_seed"] + s["ns_basecase"] for s in stats) / len(stats)
+    ns_fb = sum(s["ns_fallback"] for s in stats) / len(stats)
     ns_trav = sum(s["ns_traverse"] for s in stats) / len(stats)
     pairs = sum(s["point_pairs"] for s in stats) / len(stats)
-    flops = 3.0 * d * pairs                      # d subtractions + d fused multiply-adds
     sms = props.multi_processor_count
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 2.0 * 128 * sms * sm_max * 1e6 / 1e12      # TFLOP/s, FMA counted as 2
-    achieved = flops / (ns_tile * 1e-9) / 1e12 if ns_tile > 0 else 0.0
+    roof = roofline(args.precision, d, pairs, ns_tile, sms)
     s0 = stats[-1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -287,17 +343,14 @@ def main():
                    "step": "build ref tree + build query tree + dtree_knn",
                    "l2": "inputs (320 MB) larger than the 129 MB L2; no flush",
                    "parallelism": f"{world} GPU(s), one query shard each, reference replicated"},
-        "roofline": {"bound": "alu", "kernel": "k_tile (BaseCase, CUDA-core float32)",
-                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak if fp32_peak else None, "traffic": None,
-                     "peak_source": f"2 x 128 FP32 lanes x {sms} SMs x {sm_max:.0f} MHz",
-                     "algorithmic_flops_per_step": flops},
-        "phases_ms": {"basecase_tiles": ns_tile / 1e6, "traverse": ns_trav / 1e6,
-                      "build_and_rest": ms_max - (ns_tile + ns_trav) / 1e6},
+        "roofline": roof,
+        "phases_ms": {"basecase_tiles": ns_tile / 1e6, "fallback": ns_fb / 1e6,
+                      "traverse": ns_trav / 1e6,
+                      "build_and_rest": ms_max - (ns_tile + ns_fb + ns_trav) / 1e6},
         "counters": {k2: s0[k2] for k2 in ("node_pairs_scored", "node_pairs_pruned",
                                           "leaf_pairs_emitted", "leaf_pairs_skipped",
                                           "leaf_pairs_evaluated", "point_pairs",
-                                          "rerank_candidates", "fallback_blocks")},
+                                          "rerank_candidates", "fallback_queries")},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(W.ref.nbytes + W.query.nbytes),
                 "d2h_bytes_per_step": int(nq * k * (8 + 4))},

@@ -52,7 +52,8 @@ typedef enum dtree_status {
  * float64 (see dtree_knn). */
 typedef enum dtree_precision {
     DTREE_PREC_FP32 = 0,   /* CUDA-core float32 differences and squares */
-    DTREE_PREC_TF32 = 1,   /* tensor cores (tcgen05), TF32 inputs, FP32 accumulate */
+    DTREE_PREC_TF32 = 1,   /* tensor cores (tcgen05), TF32 inputs, FP32 accumulate
+                              (d <= 32; wider points return DTREE_ERR_UNSUPPORTED) */
     DTREE_PREC_BF16 = 2    /* tensor cores (tcgen05), BF16 inputs, FP32 accumulate */
 } dtree_precision;
 
@@ -63,10 +64,10 @@ typedef struct dtree_opts {
     int32_t query_block;   /* dtree_knn: max queries per work unit (query-tree node), 16..128
                               (default 128) */
     int32_t seed_points;   /* dtree_knn: min reference points of the seed subtree evaluated
-                              before the traversal (default 4 * leaf) */
+                              before the traversal (default 512) */
     int32_t proposal;      /* dtree_knn: 1 = use the attached learned proposal (default 0) */
-    int32_t spin_budget;   /* dtree_knn: iterations of a device-side wait before it gives up
-                              with DTREE_ERR_TIMEOUT (default 1 << 26) */
+    int32_t spin_budget;   /* dtree_knn: polls of a device-side wait before it gives up
+                              with DTREE_ERR_TIMEOUT (default 1 << 20, about a second) */
     int32_t reserved[10];  /* must be zero */
 } dtree_opts;
 
@@ -79,7 +80,8 @@ typedef struct dtree_stats {
     int64_t leaf_pairs_evaluated;/* pairs whose BaseCase tile ran (seed pairs included) */
     int64_t point_pairs;         /* BaseCase(p_q, p_r) evaluations */
     int64_t rerank_candidates;   /* candidates re-ranked in float64 */
-    int64_t fallback_blocks;     /* query blocks recomputed in float64 (band overflow) */
+    int64_t fallback_queries;    /* queries whose error band overflowed the candidate list
+                                    and were recomputed exactly in float64 */
     int64_t query_blocks;        /* work units */
     int64_t kernel_launches;     /* kernels this call launched */
     /* device time of each phase in nanoseconds, from CUDA events recorded on
@@ -87,7 +89,7 @@ typedef struct dtree_stats {
     int64_t ns_seed;             /* seed selection + seed BaseCase */
     int64_t ns_traverse;         /* bounds + dual-tree traversal + candidate lists */
     int64_t ns_basecase;         /* main BaseCase pass (tiles, re-rank, output) */
-    int64_t ns_fallback;         /* float64 recomputation of overflowed blocks */
+    int64_t ns_fallback;         /* recomputation of overflowed queries */
     int64_t reserved[2];
 } dtree_stats;
 
@@ -167,6 +169,29 @@ int64_t dtree_leaf_count(const dtree_t* tree);
  */
 int dtree_export(const dtree_t* tree, int32_t* perm, float* box, float* lambda, int32_t* begin,
                  int32_t* count, void* stream);
+
+/*
+ * dtree_debug_mma -- diagnostic: one 128 x 128 tensor-core tile through the
+ * operand layout, descriptors and TMEM read-out the BaseCase tiles use.
+ *   A, B  device, 128 x K float32 row-major (K <= 64), rounded to
+ *         `precision` (DTREE_PREC_BF16 or DTREE_PREC_TF32) on the way in
+ *   out   device, 128 x 128 float32: out[i][j] = sum_k A~[i][k] * B~[j][k]
+ *         accumulated in FP32 by tcgen05.mma
+ * Returns DTREE_ERR_UNSUPPORTED on a device other than sm_103, and
+ * DTREE_ERR_TIMEOUT if the completion wait gave up.  Waits for the result.
+ * (No counterpart in the paper: this checks the hardware path only.)
+ */
+int dtree_debug_mma(const float* A, const float* B, int32_t K, int32_t precision, float* out,
+                    void* stream);
+
+/*
+ * dtree_debug_tc_timers -- diagnostic: while `counters` (device, 32 zeroed
+ * uint64, or NULL to stop) is set, the main tensor-core BaseCase pass adds
+ * per-role clock64 cycle counts to it (window loading, stage waits, stage
+ * filling, conversion, epilogue waits and work, ...).  Process-wide; not
+ * thread-safe.  (No counterpart in the paper: a performance probe.)
+ */
+int dtree_debug_tc_timers(unsigned long long* counters);
 
 /* Static description of a status code. */
 const char* dtree_error_string(int status);

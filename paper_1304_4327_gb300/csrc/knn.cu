@@ -24,8 +24,9 @@
 //                the lists improve and skips leaves whose d_min exceeds it,
 //                then re-ranks the candidates near the k-th distance in float64
 //                and writes the outputs;
-//   5. fallback  blocks whose band of near-k-th candidates overflowed run
-//                again in float64.
+//   5. fallback  a query whose band of near-k-th candidates overflowed its
+//                list is recomputed exactly in float64 over its block's
+//                candidate leaves (one CTA per such query).
 #include <algorithm>
 #include <vector>
 
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(256) k_expand(const float* __restrict__ qbox,
                                                 const float* __restrict__ rbox,
                                                 const float* __restrict__ Bq, const int2* fin,
                                                 const int* nin, int2* fout, int* nout, int64_t cap,
-                                                int3* outp, int* noutp, int64_t capp, int* bcount,
+                                                int4* outp, int* noutp, int64_t capp, int* bcount,
                                                 int Lb, int hr, int64_t qblock0, int64_t rleaf0,
                                                 const int32_t* sl0, const int32_t* sn, int* overflow,
                                                 unsigned long long* stats) {
@@ -136,7 +137,15 @@ __global__ void __launch_bounds__(256) k_expand(const float* __restrict__ qbox,
                     if (leaf >= s0 && leaf < s0 + sn[blk]) continue;  // evaluated by the seed
                     int pos = atomicAdd(noutp, 1);
                     if (pos < capp) {
-                        outp[pos] = make_int3(blk, leaf, __float_as_int(dmin));
+                        // evaluation order: squared distance between the box centres
+                        const float* rbx = rbox + rc * 2 * DP;
+                        float o = 0.f;
+#pragma unroll
+                        for (int j = 0; j < DP; ++j) {
+                            float t = 0.5f * (qbx[j] + qbx[DP + j]) - 0.5f * (rbx[j] + rbx[DP + j]);
+                            o = fmaf(t, t, o);
+                        }
+                        outp[pos] = make_int4(blk, leaf, __float_as_int(dmin), __float_as_int(o));
                         atomicAdd(&bcount[blk], 1);
                         ++em;
                     } else {
@@ -171,9 +180,8 @@ __global__ void k_fill(float* p, int64_t n, float v) {
 // One warp per block: B_1 / A of the block from its queries' k-th keys, then
 // pushed to every ancestor with monotone atomics (non-negative floats order
 // like their bit patterns).
-__global__ void k_block_bounds(const float* cand_d, int64_t nq, int k, float ubscale,
-                               const int32_t* qbeg, const int32_t* qcnt, int64_t qblock0,
-                               int nblocks, float* B1n, float* An) {
+__global__ void k_block_bounds(const float* qub, const int32_t* qbeg, const int32_t* qcnt,
+                               int64_t qblock0, int nblocks, float* B1n, float* An) {
     int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     if (w >= nblocks) return;
@@ -181,8 +189,7 @@ __global__ void k_block_bounds(const float* cand_d, int64_t nq, int k, float ubs
     int b = qbeg[node], c = qcnt[node];
     float mx = 0.f, mn = INFINITY;
     for (int i = lane; i < c; i += 32) {
-        float kth = cand_d[(int64_t)(k - 1) * nq + b + i];
-        float ub = kth < INFINITY ? __fsqrt_ru(__fmul_ru(kth, ubscale)) : INFINITY;
+        float ub = qub[b + i];
         mx = fmaxf(mx, ub);
         mn = fminf(mn, ub);
     }
@@ -238,21 +245,22 @@ __global__ void __launch_bounds__(1024) k_scan(const int* cnt, int n, int64_t* o
     if (threadIdx.x == 0) off[n] = carry;
 }
 
-__global__ void k_csr_fill(const int3* outp, int np, const int64_t* off, int* cur, int32_t* leaf,
-                           float* dmin) {
+__global__ void k_csr_fill(const int4* outp, int np, const int64_t* off, int* cur, int32_t* leaf,
+                           float* dmin, float* key) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
-    int3 e = outp[i];
+    int4 e = outp[i];
     int64_t pos = off[e.x] + atomicAdd(&cur[e.x], 1);
     leaf[pos] = e.y;
     dmin[pos] = __int_as_float(e.z);
+    key[pos] = __int_as_float(e.w);
 }
 
 }  // namespace
 
 template <int DP>
 int launch_expand(const float* qbox, const float* rbox, const float* Bq, const int2* fin,
-                  const int* nin, int2* fout, int* nout, int64_t cap, int3* outp, int* noutp,
+                  const int* nin, int2* fout, int* nout, int64_t cap, int4* outp, int* noutp,
                   int64_t capp, int* bcount, int Lb, int hr, int64_t qblock0, int64_t rleaf0,
                   const int32_t* sl0, const int32_t* sn, int* overflow, unsigned long long* stats,
                   int grid, cudaStream_t s) {
@@ -326,7 +334,8 @@ struct Pool {
 
 template <int DP>
 int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* out_idx,
-             float* out_dist, int qb_cap, int seed_pts, cudaStream_t s, dtree_stats* st) {
+             float* out_dist, int qb_cap, int seed_pts, int prec, int spin, cudaStream_t s,
+             dtree_stats* st) {
     const int64_t launches0 = g_launches.load();
     const int64_t nq = tq->n, m = tr->n;
     const int Lb = std::min<int>(tq->height, level_of_count(nq, qb_cap));
@@ -336,16 +345,22 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
     const int cpb = (int)((maxcnt + kQB - 1) / kQB);
     const int hr = tr->height;
     const int64_t rleaf0 = ((int64_t)1 << hr) - 1;
-    int KC = 4;
-    while (KC < k + 1) KC *= 2;
-    if (KC > 32) return DTREE_ERR_UNSUPPORTED;
+    // list length: room for k plus the candidates inside the error band (the
+    // tensor-core band is wider, so its lists are longer)
+    const int fmt = prec == DTREE_PREC_BF16 ? 1 : prec == DTREE_PREC_TF32 ? 2 : 0;
+    // list length: k plus room for the candidates inside the error band
+    // (TF32 band ~1% of d^2 at d=16, BF16 ~5%); buckets 4, 8, 16, 24, 32
+    const int kc_need = fmt == 1 ? 2 * k + 12 : fmt == 2 ? k + 14 : k + 1;
+    int KC = kc_need <= 4 ? 4 : kc_need <= 8 ? 8 : kc_need <= 16 ? 16 : kc_need <= 24 ? 24 : 32;
+    if (k + 1 > 32) return DTREE_ERR_UNSUPPORTED;
     int Ls = 0;
     while (Ls < hr && (m >> (Ls + 1)) >= seed_pts) ++Ls;
 
     Pool P{s};
-    int32_t *sl0, *sn, *cand_i, *fb_list, *csr_leaf = nullptr;
-    float *cand_d, *B1n, *An, *Bn, *csr_dmin = nullptr;
-    int *ctr, *bcount, *bcur, *fb_flag;
+    int32_t *sl0, *sn, *cand_i, *csr_leaf = nullptr;
+    int4* fbq_list;
+    float *cand_d, *B1n, *An, *Bn, *csr_dmin = nullptr, *csr_key = nullptr;
+    int *ctr, *bcount, *bcur;
     int64_t* off;
     unsigned long long* dstats;
     const int64_t nqn = 2 * (int64_t)nblocks - 1;
@@ -353,18 +368,23 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
     DT_TRY(P.get(&sn, nblocks));
     DT_TRY(P.get(&cand_d, (size_t)KC * nq));
     DT_TRY(P.get(&cand_i, (size_t)KC * nq));
+    float* qub;
+    int* derr;
+    DT_TRY(P.get(&qub, nq));
+    DT_TRY(P.get(&derr, 1));
+    DT_CHECK(cudaMemsetAsync(derr, 0, sizeof(int), s));
     DT_TRY(P.get(&B1n, nqn));
     DT_TRY(P.get(&An, nqn));
     DT_TRY(P.get(&Bn, nqn));
-    DT_TRY(P.get(&ctr, 16));  // 0-2 work counters, 3 fb count, 4 overflow, 5-6 frontier, 7 pairs
+    // 0-2 work counters, 3 fb count, 4 overflow, 5-6 frontier, 7 pairs, 8 fb2 count, 9 work
+    DT_TRY(P.get(&ctr, 16));
     DT_TRY(P.get(&bcount, nblocks));
     DT_TRY(P.get(&bcur, nblocks));
-    DT_TRY(P.get(&fb_flag, nblocks));
-    DT_TRY(P.get(&fb_list, nblocks));
+    DT_TRY(P.get(&fbq_list, nq));
     DT_TRY(P.get(&off, nblocks + 1));
     DT_TRY(P.get(&dstats, ST_NSTAT));
     DT_CHECK(cudaMemsetAsync(ctr, 0, 16 * sizeof(int), s));
-    DT_CHECK(cudaMemsetAsync(fb_flag, 0, nblocks * sizeof(int), s));
+
     DT_CHECK(cudaMemsetAsync(dstats, 0, ST_NSTAT * sizeof(unsigned long long), s));
     PhaseTimer tm(s, st != nullptr);
     tm.mark();  // 0
@@ -377,6 +397,7 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
     a.qbeg = tq->nbeg;
     a.qcnt = tq->ncnt;
     a.qlam = tq->lam;
+    a.qbox = tq->box;
     a.qblock0 = qblock0;
     a.nq = nq;
     a.cpb = cpb;
@@ -384,6 +405,7 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
     a.ridx = tr->idx;
     a.rbeg = tr->nbeg;
     a.rcnt = tr->ncnt;
+    a.rbox = tr->box;
     a.rleaf0 = rleaf0;
     a.k = k;
     a.mono = mono ? 1 : 0;
@@ -391,22 +413,27 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
     a.seed_nleaf = sn;
     a.cand_d = cand_d;
     a.cand_i = cand_i;
+    a.qub = qub;
     a.nwork = nblocks;
     a.out_idx = out_idx;
     a.out_dist = out_dist;
-    a.fb_flag = fb_flag;
-    a.fb_list = fb_list;
-    a.fb_count = ctr + 3;
+    a.fbq_list = fbq_list;
+    a.fbq_count = ctr + 3;
     a.stats = dstats;
     a.work_ctr = ctr + 0;
-    DT_TRY(launch_tile_cc<DP>(a, KC, MODE_SEED, nblocks * cpb, s));
+    auto tile = [&](int mode, int items) -> int {
+        if (fmt)
+            return launch_tile_tc<DP>(a, fmt, KC, mode, items, derr, spin, s);
+        return launch_tile_cc<DP>(a, KC, mode, items, s);
+    };
+    DT_TRY(tile(MODE_SEED, nblocks * cpb));
     tm.mark();  // 1
 
     // 2. bounds of every query node down to the blocks
     DT_LAUNCH(k_fill, (int)((nqn + 255) / 256), 256, 0, s, B1n, nqn, 0.f);
     DT_LAUNCH(k_fill, (int)((nqn + 255) / 256), 256, 0, s, An, nqn, INFINITY);
-    DT_LAUNCH(k_block_bounds, (nblocks * 32 + 255) / 256, 256, 0, s, cand_d, nq, k,
-              1.f + 2.f * rel_eps<DP>(), tq->nbeg, tq->ncnt, qblock0, nblocks, B1n, An);
+    DT_LAUNCH(k_block_bounds, (nblocks * 32 + 255) / 256, 256, 0, s, qub, tq->nbeg, tq->ncnt,
+              qblock0, nblocks, B1n, An);
     DT_LAUNCH(k_node_bounds, (int)((nqn + 255) / 256), 256, 0, s, B1n, An, tq->lam, nqn, Bn);
 
     // 3. level-synchronous pruning dual-tree traversal
@@ -416,7 +443,7 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
     int np = 0;
     for (int attempt = 0;; ++attempt) {
         int2 *F0, *F1;
-        int3* outp;
+        int4* outp;
         DT_TRY(P.get(&F0, cap));
         DT_TRY(P.get(&F1, cap));
         DT_TRY(P.get(&outp, cap));
@@ -447,11 +474,12 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
             np = hp;
             DT_TRY(P.get(&csr_leaf, std::max(np, 1)));
             DT_TRY(P.get(&csr_dmin, std::max(np, 1)));
+            DT_TRY(P.get(&csr_key, std::max(np, 1)));
             DT_LAUNCH(k_scan, 1, 1024, 0, s, bcount, nblocks, off);
             DT_CHECK(cudaMemsetAsync(bcur, 0, nblocks * sizeof(int), s));
             if (np > 0)
                 DT_LAUNCH(k_csr_fill, (np + 255) / 256, 256, 0, s, outp, np, off, bcur, csr_leaf,
-                          csr_dmin);
+                          csr_dmin, csr_key);
             P.release(outp);
             break;
         }
@@ -468,21 +496,19 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
     a.csr_off = off;
     a.csr_leaf = csr_leaf;
     a.csr_dmin = csr_dmin;
+    a.csr_key = csr_key;
     a.Bq = Bn + qblock0;
     a.work_ctr = ctr + 1;
-    DT_TRY(launch_tile_cc<DP>(a, KC, MODE_MAIN, nblocks * cpb, s));
+    DT_TRY(tile(MODE_MAIN, nblocks * cpb));
     tm.mark();  // 3
-    int nfb = 0;
+    int nfb = 0, herr = 0;
     DT_CHECK(cudaMemcpyAsync(&nfb, ctr + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DT_CHECK(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
     DT_CHECK(cudaStreamSynchronize(s));
+    if (herr) return DTREE_ERR_TIMEOUT;
 
-    // 5. float64 recomputation of overflowed blocks
-    if (nfb > 0) {
-        a.work_blocks = fb_list;
-        a.nwork = nfb;
-        a.work_ctr = ctr + 2;
-        DT_TRY(launch_tile_cc<DP>(a, KC, MODE_FB, nfb * cpb, s));
-    }
+    // 5. exact float64 recomputation of the queries whose band overflowed
+    if (nfb > 0) DT_TRY(launch_query_fb<DP>(a, KC, nfb, s));
     tm.mark();  // 4
     unsigned long long hs[ST_NSTAT];
     DT_CHECK(cudaMemcpyAsync(hs, dstats, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -496,7 +522,7 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
         st->leaf_pairs_evaluated = (int64_t)hs[ST_EVALUATED];
         st->point_pairs = (int64_t)hs[ST_POINT_PAIRS];
         st->rerank_candidates = (int64_t)hs[ST_RERANK];
-        st->fallback_blocks = nfb;
+        st->fallback_queries = nfb;
         st->query_blocks = nblocks;
         st->kernel_launches = g_launches.load() - launches0;
         st->ns_seed = tm.ns(0, 1);
@@ -528,19 +554,26 @@ extern "C" int dtree_knn(const dtree_t* query, const dtree_t* ref, int32_t k, in
     int qb = (o && o->query_block) ? o->query_block : 128;
     if (qb < 16 || qb > 128) return DTREE_ERR_INVALID_ARG;
     if (o && o->proposal) return DTREE_ERR_NOT_TRAINED;
-    if (prec != DTREE_PREC_FP32) return DTREE_ERR_UNSUPPORTED;
-    int seed = std::max<int>(k + 1, (o && o->seed_points > 0) ? o->seed_points : 96);
+    int seed = std::max<int>(k + 1, (o && o->seed_points > 0) ? o->seed_points : 512);
+    int spin = (o && o->spin_budget > 0) ? o->spin_budget : (1 << 20);
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0;
     cudaGetDevice(&dev);
     dt::prepare_pool(dev);
+    if (prec != DTREE_PREC_FP32) {
+        // the tensor-core tiles are built for sm_103a (tcgen05)
+        int major = 0, minor = 0;
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+        if (major != 10 || minor != 3) return DTREE_ERR_UNSUPPORTED;
+    }
     int rc;
     switch (ref->dp) {
-        case 4: rc = dt::knn_impl<4>(tq, ref, mono, k, out_idx, out_dist, qb, seed, s, st); break;
-        case 8: rc = dt::knn_impl<8>(tq, ref, mono, k, out_idx, out_dist, qb, seed, s, st); break;
-        case 16: rc = dt::knn_impl<16>(tq, ref, mono, k, out_idx, out_dist, qb, seed, s, st); break;
-        case 32: rc = dt::knn_impl<32>(tq, ref, mono, k, out_idx, out_dist, qb, seed, s, st); break;
-        default: rc = dt::knn_impl<64>(tq, ref, mono, k, out_idx, out_dist, qb, seed, s, st); break;
+        case 4: rc = dt::knn_impl<4>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st); break;
+        case 8: rc = dt::knn_impl<8>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st); break;
+        case 16: rc = dt::knn_impl<16>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st); break;
+        case 32: rc = dt::knn_impl<32>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st); break;
+        default: rc = dt::knn_impl<64>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st); break;
     }
     if (rc != DTREE_OK) cudaStreamSynchronize(s);
     return rc;

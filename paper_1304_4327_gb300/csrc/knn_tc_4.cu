@@ -1,0 +1,6 @@
+// knn_tc_4.cu -- tensor-core BaseCase tiles for dimension bucket DP = 4.
+#include "knn_tc.cuh"
+
+namespace dt {
+template int launch_tile_tc<4>(const TileArgs&, int, int, int, int, int*, int, cudaStream_t);
+}  // namespace dt

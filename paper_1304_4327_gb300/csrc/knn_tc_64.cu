@@ -1,0 +1,6 @@
+// knn_tc_64.cu -- tensor-core BaseCase tiles for dimension bucket DP = 64.
+#include "knn_tc.cuh"
+
+namespace dt {
+template int launch_tile_tc<64>(const TileArgs&, int, int, int, int, int*, int, cudaStream_t);
+}  // namespace dt

@@ -17,8 +17,8 @@
 //     with the exact float64 distance (the same left-to-right sum as the
 //     definition) and ordered by (distance, reference index).
 // If more than KC - k keys fall inside the band (near-ties or duplicates) the
-// list may have dropped a true neighbour: the block is flagged and
-// recomputed in float64 (MODE_FB), where keys are exact.
+// list may have dropped a true neighbour: that query is listed and
+// recomputed in float64 (k_query_fb), where keys are exact.
 #pragma once
 
 #include "knn_common.cuh"
@@ -42,6 +42,29 @@ __device__ __forceinline__ void list_insert(T (&ld)[KC], int (&li)[KC], T d, int
             li[j] = i;
             d = td;
             i = ti;
+        }
+    }
+}
+
+// The same insertion without a serial chain: every comparison against the
+// new key is independent (the list is sorted, so the smaller entries form a
+// prefix), then each slot either keeps its entry, takes the new one or takes
+// its predecessor.  Descending order reads each predecessor before it moves.
+template <typename T, int KC>
+__device__ __forceinline__ void list_insert_par(T (&ld)[KC], int (&li)[KC], T d, int i) {
+    bool lt[KC];
+#pragma unroll
+    for (int j = 0; j < KC; ++j) lt[j] = key_less(ld[j], li[j], d, i);
+#pragma unroll
+    for (int j = KC - 1; j >= 0; --j) {
+        if (!lt[j]) {
+            if (j == 0 || lt[j - 1]) {
+                ld[j] = d;
+                li[j] = i;
+            } else {
+                ld[j] = ld[j - 1];
+                li[j] = li[j - 1];
+            }
         }
     }
 }
@@ -75,13 +98,134 @@ __device__ __forceinline__ float ub_of(T kth) {
     return __fsqrt_ru(__fmul_ru((float)kth, 1.f + 2.f * rel_eps<DP>()));
 }
 
+// Warp 0 of a tile CTA: take candidate leaves from the current window, in
+// order, skip those whose d_min exceeds the block's bound (Algorithm 3:
+// Score = infinity), and pack the rows of the rest (whole leaves, or the
+// part of a leaf that fits) into a stage of at most TN points.  stab gets one
+// (first row, rows, stage offset) entry per run of rows.
+template <int TN, int MODE>
+__device__ __forceinline__ void stage_fill(const TileArgs& a, const uint64_t* scand, int64_t w0,
+                                           int wn, int nseed, int sleaf0, int64_t c0, int3* stab,
+                                           unsigned long long& n_skip, unsigned long long& n_eval,
+                                           int& s_cur, int& s_part, int& s_nst, int& s_ntab,
+                                           const float Bc) {
+    const int lane = threadIdx.x & 31;
+    int cur = s_cur, part = s_part, nst = 0, ntab = 0;
+    while (cur < wn && nst < TN) {
+        int c = cur + lane;
+        bool valid = c < wn;
+        int leaf = 0;
+        float dmin = 0.f;
+        if (valid) {
+            if (MODE == MODE_MAIN) {
+                const int64_t ci = c0 + w0 + (uint32_t)scand[c];
+                leaf = a.csr_leaf[ci];
+                dmin = a.csr_dmin[ci];
+            } else {
+                int64_t ci = w0 + c;
+                if (ci < nseed) {
+                    leaf = sleaf0 + (int)ci;
+                } else {
+                    leaf = a.csr_leaf[c0 + ci - nseed];
+                    dmin = a.csr_dmin[c0 + ci - nseed];
+                }
+            }
+        }
+        bool keep = valid && !(dmin > Bc);
+        int lb = 0, lc = 0;
+        if (keep) {
+            int64_t ln = a.rleaf0 + leaf;
+            lb = a.rbeg[ln];
+            lc = a.rcnt[ln];
+        }
+        if (lane == 0 && part > 0 && keep) {  // rest of a split leaf
+            lb += part;
+            lc -= part;
+        }
+        int incl = lc;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        int excl = incl - lc;
+        int take = min(max(TN - nst - excl, 0), lc);
+        bool full = valid && take == lc;
+        unsigned fm = __ballot_sync(0xffffffffu, full);
+        int nlead = fm == 0xffffffffu ? 32 : __ffs(~fm) - 1;
+        bool put = take > 0 && lane <= nlead;
+        unsigned tm = __ballot_sync(0xffffffffu, put);
+        if (put) stab[ntab + __popc(tm & ((1u << lane) - 1u))] = make_int3(lb, take, nst + excl);
+        unsigned sk = __ballot_sync(0xffffffffu, valid && !keep && lane < nlead);
+        unsigned ev = __ballot_sync(0xffffffffu, keep && lane < nlead);
+        if (lane == 0) {
+            n_skip += __popc(sk);
+            n_eval += __popc(ev);
+        }
+        int taken = put ? take : 0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) taken += __shfl_xor_sync(0xffffffffu, taken, off);
+        int pn = __shfl_sync(0xffffffffu, take, nlead & 31);
+        nst += taken;
+        ntab += __popc(tm);
+        if (nlead < 32) {
+            part = (nlead == 0 ? part : 0) + pn;
+            cur += nlead;
+            if (!(cur < wn)) part = 0;
+            break;  // stage full, or the window is exhausted
+        }
+        cur += 32;
+        part = 0;
+    }
+    if (lane == 0) {
+        s_cur = cur;
+        s_part = part;
+        s_nst = nst;
+        s_ntab = ntab;
+    }
+}
+
+__device__ __forceinline__ void group_sync(int bar, int n) {
+    if (bar == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(n) : "memory");
+}
+
+// Sort the window [w0, w0 + wn) of a block's candidate list by its order key
+// (window index in the low bits) into scand: bitonic sort by the NT threads of a group
+// (thread index tid within it, barrier BAR; 0 = the whole CTA).
+template <int NT, int BAR = 0>
+__device__ __forceinline__ void sort_window(const TileArgs& a, int64_t c0, int64_t w0, int wn,
+                                            uint64_t* scand, int tid = threadIdx.x) {
+    int np2 = 1;
+    while (np2 < wn) np2 <<= 1;
+    for (int i = tid; i < np2; i += NT) {
+        uint64_t key = ~0ull;
+        if (i < wn) key = ((uint64_t)f2o(a.csr_key[c0 + w0 + i]) << 32) | (uint32_t)i;
+        scand[i] = key;
+    }
+    group_sync(BAR, NT);
+    for (int kk = 2; kk <= np2; kk <<= 1)
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int t = tid; t < np2 / 2; t += NT) {
+                int i = 2 * t - (t & (jj - 1));
+                int l = i + jj;
+                bool up = (i & kk) == 0;
+                uint64_t x = scand[i], y = scand[l];
+                if ((x > y) == up) {
+                    scand[i] = y;
+                    scand[l] = x;
+                }
+            }
+            group_sync(BAR, NT);
+        }
+}
+
 template <typename T, int DP, int KC, int MODE>
 __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
     constexpr int TN = 4096 / DP;       // staged reference points (16 KB)
     constexpr int SORTCAP = 2048;       // candidates sorted per window
     __shared__ __align__(16) float rs[TN * DP];
     __shared__ int32_t spos[TN];
-    __shared__ int32_t sorig[MODE == MODE_FB ? TN : 1];
     __shared__ uint64_t scand[MODE == MODE_MAIN ? SORTCAP : 1];
     __shared__ int3 stab[TN];
     __shared__ int s_item, s_ntab, s_nst, s_cur, s_part;
@@ -165,33 +309,7 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
 
             for (int64_t w0 = 0; w0 < ntot; w0 += win) {
                 const int wn = (int)(ntot - w0 < win ? ntot - w0 : win);
-                if (MODE == MODE_MAIN) {
-                    int np2 = 1;
-                    while (np2 < wn) np2 <<= 1;
-                    for (int i = tid; i < np2; i += kQB) {
-                        uint64_t key = ~0ull;
-                        if (i < wn) {
-                            int64_t ci = c0 + w0 + i;
-                            key = ((uint64_t)f2o(a.csr_dmin[ci]) << 32) | (uint32_t)a.csr_leaf[ci];
-                        }
-                        scand[i] = key;
-                    }
-                    __syncthreads();
-                    for (int kk = 2; kk <= np2; kk <<= 1)
-                        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-                            for (int t = tid; t < np2 / 2; t += kQB) {
-                                int i = 2 * t - (t & (jj - 1));
-                                int l = i + jj;
-                                bool up = (i & kk) == 0;
-                                uint64_t x = scand[i], y = scand[l];
-                                if ((x > y) == up) {
-                                    scand[i] = y;
-                                    scand[l] = x;
-                                }
-                            }
-                            __syncthreads();
-                        }
-                }
+                if (MODE == MODE_MAIN) sort_window<kQB>(a, c0, w0, wn, scand);
                 if (tid == 0) {
                     s_cur = 0;
                     s_part = 0;
@@ -199,82 +317,9 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
                 __syncthreads();
                 while (s_cur < wn) {
                     // ---- warp 0 fills the stage with whole or partial leaves
-                    if (warp == 0) {
-                        int cur = s_cur, part = s_part, nst = 0, ntab = 0;
-                        const float Bc = s_B;
-                        while (cur < wn && nst < TN) {
-                            int c = cur + lane;
-                            bool valid = c < wn;
-                            int leaf = 0;
-                            float dmin = 0.f;
-                            if (valid) {
-                                if (MODE == MODE_MAIN) {
-                                    uint64_t key = scand[c];
-                                    leaf = (int)(uint32_t)key;
-                                    dmin = o2f((uint32_t)(key >> 32));
-                                } else {
-                                    int64_t ci = w0 + c;
-                                    if (ci < nseed) {
-                                        leaf = sleaf0 + (int)ci;
-                                    } else {
-                                        leaf = a.csr_leaf[c0 + ci - nseed];
-                                        dmin = a.csr_dmin[c0 + ci - nseed];
-                                    }
-                                }
-                            }
-                            bool keep = valid && !(dmin > Bc);
-                            int lb = 0, lc = 0;
-                            if (keep) {
-                                int64_t ln = a.rleaf0 + leaf;
-                                lb = a.rbeg[ln];
-                                lc = a.rcnt[ln];
-                            }
-                            if (lane == 0 && part > 0 && keep) {  // rest of a split leaf
-                                lb += part;
-                                lc -= part;
-                            }
-                            int incl = lc;
-#pragma unroll
-                            for (int off = 1; off < 32; off <<= 1) {
-                                int v = __shfl_up_sync(0xffffffffu, incl, off);
-                                if (lane >= off) incl += v;
-                            }
-                            int excl = incl - lc;
-                            int take = min(max(TN - nst - excl, 0), lc);
-                            bool full = valid && take == lc;
-                            unsigned fm = __ballot_sync(0xffffffffu, full);
-                            int nlead = fm == 0xffffffffu ? 32 : __ffs(~fm) - 1;
-                            bool put = take > 0 && lane <= nlead;
-                            unsigned tm = __ballot_sync(0xffffffffu, put);
-                            if (put) stab[ntab + __popc(tm & ((1u << lane) - 1u))] = make_int3(lb, take, nst + excl);
-                            unsigned sk = __ballot_sync(0xffffffffu, valid && !keep && lane < nlead);
-                            unsigned ev = __ballot_sync(0xffffffffu, keep && lane < nlead);
-                            if (lane == 0) {
-                                n_skip += __popc(sk);
-                                n_eval += __popc(ev);
-                            }
-                            int taken = put ? take : 0;
-#pragma unroll
-                            for (int off = 16; off > 0; off >>= 1) taken += __shfl_xor_sync(0xffffffffu, taken, off);
-                            int pn = __shfl_sync(0xffffffffu, take, nlead & 31);
-                            nst += taken;
-                            ntab += __popc(tm);
-                            if (nlead < 32) {
-                                part = (nlead == 0 ? part : 0) + pn;
-                                cur += nlead;
-                                if (!(cur < wn)) part = 0;
-                                break;  // stage full, or the window is exhausted
-                            }
-                            cur += 32;
-                            part = 0;
-                        }
-                        if (lane == 0) {
-                            s_cur = cur;
-                            s_part = part;
-                            s_nst = nst;
-                            s_ntab = ntab;
-                        }
-                    }
+                    if (warp == 0)
+                        stage_fill<TN, MODE>(a, scand, w0, wn, nseed, sleaf0, c0, stab, n_skip,
+                                             n_eval, s_cur, s_part, s_nst, s_ntab, s_B);
                     __syncthreads();
                     // ---- all warps copy the staged rows
                     const int ntab = s_ntab, nst = s_nst;
@@ -285,7 +330,6 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
                         for (int f = lane; f < e.y * (DP / 4); f += 32) dst[f] = src[f];
                         for (int i = lane; i < e.y; i += 32) {
                             spos[e.z + i] = e.x + i;
-                            if (MODE == MODE_FB) sorig[e.z + i] = a.ridx[e.x + i];
                         }
                     }
                     __syncthreads();
@@ -319,7 +363,7 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
                                 }
                             }
                             const int rp = spos[e];
-                            const int tie = MODE == MODE_FB ? sorig[e] : rp;
+                            const int tie = rp;
                             if (key_less(acc, tie, ld[KC - 1], li[KC - 1]) && !(a.mono && rp == myq))
                                 list_insert(ld, li, acc, tie);
                         }
@@ -338,24 +382,15 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
                         a.cand_d[(int64_t)j * a.nq + myq] = (float)ld[j];
                         a.cand_i[(int64_t)j * a.nq + myq] = li[j];
                     }
-                }
-            } else if (MODE == MODE_FB) {
-                if (act) {
-                    int64_t base = (int64_t)a.qidx[myq] * a.k;
-#pragma unroll
-                    for (int j = 0; j < KC; ++j)
-                        if (j < a.k) {
-                            a.out_idx[base + j] = li[j];
-                            a.out_dist[base + j] = (float)sqrt((double)ld[j]);
-                        }
+                    a.qub[myq] = ub_of<T, DP>(list_at(ld, a.k - 1));
                 }
             } else {
                 const float kth = (float)list_at(ld, a.k - 1);
                 const float band = __fmul_ru(kth, 1.f + 4.f * rel_eps<DP>());
                 const bool ovf = act && li[KC - 1] != kEmptyIdx && !((float)ld[KC - 1] > band);
-                if (__syncthreads_or(ovf)) {
-                    if (tid == 0 && atomicExch(&a.fb_flag[blk], 1) == 0)
-                        a.fb_list[atomicAdd(a.fb_count, 1)] = blk;
+                if (ovf) {
+                    a.fbq_list[atomicAdd(a.fbq_count, 1)] =
+                        make_int4(myq, blk, __float_as_int(ub_of<T, DP>(list_at(ld, a.k - 1))), 0);
                 } else if (act) {
                     double rd[KC];
                     int ri[KC];
@@ -400,6 +435,164 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
     if (n_re) atomicAdd(&a.stats[ST_RERANK], n_re);
 }
 
+// Exact recomputation of one query whose error band overflowed its list, one
+// CTA per query.  The candidate leaves are its block's seed leaves and
+// traversal candidates; each is kept only if the distance from the query to
+// the leaf's box (rounded down) does not exceed the query's upper bound on its
+// k-th distance (the single-tree form of Algorithm 3's Score), so the work
+// follows the query's own ball, not its block's.  Kept leaves gather in a
+// shared buffer; when it fills, the 128 threads evaluate its points, one
+// point each in turn, in exact float64, each keeping a (distance, index)
+// list; thread 0 merges the 128 sorted lists.
+constexpr int kFbLeafBuf = 512;
+
+template <int DP>
+__device__ __forceinline__ float point_box_dmin_down(const float* q, const float* bx) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < DP; ++j) {
+        float g = fmaxf(fmaxf(bx[j] - q[j], q[j] - bx[DP + j]), 0.f);
+        s = fmaf(g, g, s);
+    }
+    return __fmul_rd(__fsqrt_rd(s), 1.f - rel_eps<DP>());
+}
+
+template <int DP, int KC>
+__global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    double* md = reinterpret_cast<double*>(fsm);                 // KC x 128
+    int32_t* mi = reinterpret_cast<int32_t*>(md + KC * kQB);     // KC x 128
+    __shared__ int s_lb[kFbLeafBuf], s_pre[kFbLeafBuf + 1];
+    __shared__ int s_n;
+    const int4 e = a.fbq_list[blockIdx.x];
+    const int myq = e.x, blk = e.y;
+    const float ub = __int_as_float(e.z);
+    const int tid = threadIdx.x;
+    float q[DP];
+    {
+        const float4* q4 = reinterpret_cast<const float4*>(a.qpts + (int64_t)myq * DP);
+#pragma unroll
+        for (int j = 0; j < DP / 4; ++j) {
+            float4 v = q4[j];
+            q[4 * j] = v.x;
+            q[4 * j + 1] = v.y;
+            q[4 * j + 2] = v.z;
+            q[4 * j + 3] = v.w;
+        }
+    }
+    double ld[KC];
+    int li[KC];
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+        ld[j] = (double)INFINITY;
+        li[j] = kEmptyIdx;
+    }
+    const int nseed = a.seed_nleaf[blk], sleaf0 = a.seed_leaf0[blk];
+    const int64_t c0 = a.csr_off[blk], c1 = a.csr_off[blk + 1];
+    const int64_t ntot = nseed + (c1 - c0);
+    if (tid == 0) s_n = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < ntot; base += kQB) {
+        // 1. test one candidate leaf per thread against the query's ball
+        const int64_t c = base + tid;
+        int leaf = -1;
+        if (c < ntot) {
+            if (c < nseed) {
+                leaf = sleaf0 + (int)c;
+            } else if (!(a.csr_dmin[c0 + c - nseed] > ub)) {
+                leaf = a.csr_leaf[c0 + c - nseed];
+            }
+            if (leaf >= 0 && point_box_dmin_down<DP>(q, a.rbox + (a.rleaf0 + leaf) * 2 * DP) > ub)
+                leaf = -1;
+        }
+        if (leaf >= 0) s_lb[atomicAdd(&s_n, 1)] = leaf;
+        __syncthreads();
+        // 2. evaluate the buffered leaves once the next round might not fit
+        const int nb = s_n;
+        const bool flush = nb > 0 && (base + kQB >= ntot || nb + kQB > kFbLeafBuf);
+        __syncthreads();  // every thread has read s_n before the next round adds to it
+        if (flush) {
+            if (tid == 0) {
+                int acc = 0;
+                for (int i = 0; i < nb; ++i) {
+                    s_pre[i] = acc;
+                    acc += a.rcnt[a.rleaf0 + s_lb[i]];
+                }
+                s_pre[nb] = acc;
+            }
+            __syncthreads();
+            const int npts = s_pre[nb];
+            for (int p = tid; p < npts; p += kQB) {
+                int lo = 0, hi = nb - 1;  // the buffered leaf holding point p
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_pre[mid] <= p) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int r = a.rbeg[a.rleaf0 + s_lb[lo]] + (p - s_pre[lo]);
+                if (a.mono && r == myq) continue;
+                const double d2 = exact_d2<DP>(q, a.rpts + (int64_t)r * DP);
+                const int orig = a.ridx[r];
+                if (key_less(d2, orig, ld[KC - 1], li[KC - 1])) list_insert(ld, li, d2, orig);
+            }
+            __syncthreads();
+            if (tid == 0) s_n = 0;
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+        md[j * kQB + tid] = ld[j];
+        mi[j * kQB + tid] = li[j];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int head[kQB];
+        for (int t = 0; t < kQB; ++t) head[t] = 0;
+        const int64_t base = (int64_t)a.qidx[myq] * a.k;
+        for (int j = 0; j < a.k; ++j) {
+            int best = -1;
+            double bd = (double)INFINITY;
+            int bi = kEmptyIdx;
+            for (int t = 0; t < kQB; ++t) {
+                if (head[t] >= KC) continue;
+                const double d = md[head[t] * kQB + t];
+                const int i = mi[head[t] * kQB + t];
+                if (best < 0 || key_less(d, i, bd, bi)) {
+                    best = t;
+                    bd = d;
+                    bi = i;
+                }
+            }
+            head[best]++;
+            a.out_idx[base + j] = bi;
+            a.out_dist[base + j] = (float)sqrt(bd);
+        }
+    }
+}
+
+template <int DP>
+int launch_query_fb(const TileArgs& a, int kc, int nfbq, cudaStream_t s) {
+#define DT_FB_CASE(KCV)                                                                       \
+    case KCV: {                                                                               \
+        const size_t smem = (size_t)KCV * kQB * 12;                                           \
+        DT_CHECK(cudaFuncSetAttribute(k_query_fb<DP, KCV>,                                    \
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        DT_LAUNCH((k_query_fb<DP, KCV>), nfbq, kQB, smem, s, a);                              \
+        return DTREE_OK;                                                                      \
+    }
+    switch (kc) {
+        DT_FB_CASE(4)
+        DT_FB_CASE(8)
+        DT_FB_CASE(16)
+        DT_FB_CASE(24)
+        DT_FB_CASE(32)
+        default:
+            return DTREE_ERR_UNSUPPORTED;
+    }
+#undef DT_FB_CASE
+}
+
 template <class K>
 inline int tile_grid(K kern, int items) {
     int g = occupancy_grid((const void*)kern, kQB, 0);
@@ -416,15 +609,13 @@ int launch_tile_cc(const TileArgs& a, int kc, int mode, int items, cudaStream_t 
         } else if (mode == MODE_MAIN) {                                                   \
             auto kern = k_tile<float, DP, KCV, MODE_MAIN>;                                \
             DT_LAUNCH(kern, tile_grid(kern, items), kQB, 0, s, a);                        \
-        } else {                                                                          \
-            auto kern = k_tile<double, DP, KCV, MODE_FB>;                                 \
-            DT_LAUNCH(kern, tile_grid(kern, items), kQB, 0, s, a);                        \
         }                                                                                 \
         return DTREE_OK;
     switch (kc) {
         DT_TILE_CASE(4)
         DT_TILE_CASE(8)
         DT_TILE_CASE(16)
+        DT_TILE_CASE(24)
         DT_TILE_CASE(32)
         default:
             return DTREE_ERR_UNSUPPORTED;

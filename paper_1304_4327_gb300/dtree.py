@@ -29,7 +29,7 @@ class dtree_opts(ctypes.Structure):
 
 STAT_FIELDS = ("node_pairs_scored", "node_pairs_pruned", "leaf_pairs_emitted",
                "leaf_pairs_skipped", "leaf_pairs_evaluated", "point_pairs",
-               "rerank_candidates", "fallback_blocks", "query_blocks", "kernel_launches",
+               "rerank_candidates", "fallback_queries", "query_blocks", "kernel_launches",
                "ns_seed", "ns_traverse", "ns_basecase", "ns_fallback")
 
 
@@ -65,6 +65,10 @@ def _load() -> ctypes.CDLL:
     lib.dtree_export.argtypes = [_P, _P, _P, _P, _P, _P, _P]
     lib.dtree_error_string.argtypes = [ctypes.c_int]
     lib.dtree_error_string.restype = ctypes.c_char_p
+    lib.dtree_debug_mma.argtypes = [_P, _P, _I32, _I32, _P, _P]
+    lib.dtree_debug_mma.restype = ctypes.c_int
+    lib.dtree_debug_tc_timers.argtypes = [_P]
+    lib.dtree_debug_tc_timers.restype = ctypes.c_int
     lib.dtree_launch_count.argtypes = []
     lib.dtree_launch_count.restype = _I64
     for f in (lib.dtree_build, lib.dtree_knn, lib.dtree_export):
@@ -217,3 +221,28 @@ def knn(ref_points: torch.Tensor, query_points: Optional[torch.Tensor], k: int,
         tr.free()
         if tq is not None:
             tq.free()
+
+
+def dtree_debug_mma(A: torch.Tensor, B: torch.Tensor, fmt: str = "bf16", stream=None) -> torch.Tensor:
+    """One 128 x 128 tensor-core tile, A (128, K) times B (128, K)^T (diagnostic)."""
+    A = _check_points(A, "A")
+    B = _check_points(B, "B")
+    out = torch.empty((128, 128), dtype=torch.float32, device=A.device)
+    rc = _lib.dtree_debug_mma(ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                              A.shape[1], PRECISIONS[fmt], ctypes.c_void_p(out.data_ptr()),
+                              _stream(stream))
+    if rc != DTREE_OK:
+        raise DTreeError(rc, "dtree_debug_mma")
+    return out
+
+
+TC_TIMERS = ("plan_window", "plan_wait", "plan_stage", "conv_wait_raw", "conv_wait_slot",
+             "conv_work", "epi_wait", "epi_work", "epi_rare_chunks", "epi_finish", "item_setup",
+             "epi_tmem", "epi_hot", "epi_rare_cycles", "epi_tail", "epi_flush", "tiles", "items")
+
+
+def dtree_debug_tc_timers(buf: Optional[torch.Tensor]) -> None:
+    """Attach (or with None detach) a zeroed int64 CUDA tensor of 32 counters."""
+    if buf is not None and (buf.numel() < 32 or buf.dtype != torch.int64 or not buf.is_cuda):
+        raise ValueError("the timer buffer must be a CUDA int64 tensor of at least 32 entries")
+    _lib.dtree_debug_tc_timers(None if buf is None else ctypes.c_void_p(buf.data_ptr()))
