@@ -42,8 +42,10 @@ typedef enum dtree_status {
     DTREE_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up (the kernel
                                     recorded it and returned; the context stays usable) */
     DTREE_ERR_NOT_TRAINED = -6,  /* a learned proposal was requested without a model */
-    DTREE_ERR_UNSUPPORTED = -7   /* valid request this build/device cannot serve
+    DTREE_ERR_UNSUPPORTED = -7,  /* valid request this build/device cannot serve
                                     (e.g. tensor-core precision on a non-sm_103 device) */
+    DTREE_ERR_TOO_LARGE = -8     /* the problem exceeds the fixed scratch of
+                                    dtree_knn_noalloc (see its limits) */
 } dtree_status;
 
 /* Distance arithmetic of the BaseCase tiles.  Whatever the choice, results
@@ -146,6 +148,42 @@ int dtree_build(const float* pts, int64_t n, int32_t d, const dtree_opts* opts, 
 int dtree_knn(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_idx,
               float* out_dist, const dtree_opts* opts, void* stream, dtree_stats* stats);
 
+/*
+ * dtree_knn_noalloc -- dtree_knn with no device allocation: the same search,
+ * arguments, results and status codes, but every scratch buffer the call
+ * needs is carved from one file-scope static device array of
+ * DTREE_NOALLOC_SCRATCH_BYTES bytes instead of the stream-ordered pool.  The
+ * paper has no counterpart; this serves callers that must not allocate (a
+ * serving loop with a fixed memory budget, or a caller whose allocator must
+ * not be touched).  The call makes no cudaMalloc/cudaFree or other
+ * allocating call; the trees and the outputs are the caller's.
+ *
+ * Limits (checked before any work; beyond them it returns
+ * DTREE_ERR_TOO_LARGE):
+ *   - at most DTREE_NOALLOC_MAX_QUERIES queries (the query tree's points, or
+ *     the reference tree's points in the monochromatic problem);
+ *   - the traversal's candidate pairs must fit what is left of the array
+ *     after the per-query buffers (checked on the device, before the pairs
+ *     are used; the call then returns DTREE_ERR_TOO_LARGE).
+ * `stats` is not offered (the phase timers would create CUDA events).
+ *
+ * The array's address on the current device is looked up once per device
+ * (cudaGetSymbolAddress, with that device current) and cached.  The trees
+ * must live on the current device (else DTREE_ERR_INVALID_ARG).
+ *
+ * The array keeps whatever the previous call left in it; every buffer whose
+ * contents must start at zero (work counters, per-block pair counts,
+ * statistics, the error word) is cleared on `stream` by the call itself.
+ *
+ * Concurrency: there is one array per device.  Calls that overlap in time
+ * on one device (different streams, or different host threads) share it and
+ * race; callers must serialise them.
+ */
+#define DTREE_NOALLOC_SCRATCH_BYTES (128u << 20)
+#define DTREE_NOALLOC_MAX_QUERIES 65536
+int dtree_knn_noalloc(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_idx,
+                      float* out_dist, const dtree_opts* opts, void* stream);
+
 /* dtree_free -- release every device allocation of the handle.  NULL-safe.
  * Must not be called while work that uses the handle is still in flight. */
 void dtree_free(dtree_t* tree);
@@ -198,6 +236,10 @@ const char* dtree_error_string(int status);
 
 /* Kernels launched by this library since the process started (all threads). */
 int64_t dtree_launch_count(void);
+
+/* Device allocations the library has made so far (tree storage and per-call
+ * scratch), for tests. */
+int64_t dtree_alloc_count(void);
 
 #ifdef __cplusplus
 }

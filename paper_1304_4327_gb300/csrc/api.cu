@@ -6,6 +6,7 @@
 namespace dt {
 
 std::atomic<int64_t> g_launches{0};
+std::atomic<int64_t> g_allocs{0};
 
 int cuda_status(cudaError_t e) {
     if (e == cudaErrorMemoryAllocation) {
@@ -53,10 +54,13 @@ int64_t dtree_leaf_count(const dtree_t* t) { return t ? t->nleaves : -1; }
 
 int64_t dtree_launch_count(void) { return dt::g_launches.load(); }
 
+int64_t dtree_alloc_count(void) { return dt::g_allocs.load(); }
+
 const char* dtree_error_string(int status) {
     switch (status) {
         case DTREE_OK: return "success";
         case DTREE_ERR_INVALID_ARG: return "invalid argument";
+        case DTREE_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of the no-allocation entry point";
         case DTREE_ERR_INVALID_K: return "invalid k (need 0 < k < m, or k <= m - 1 monochromatic)";
         case DTREE_ERR_CUDA: return "CUDA error";
         case DTREE_ERR_OOM: return "out of device memory";

@@ -596,6 +596,7 @@ int build_impl(dtree_t* t, const float* in, cudaStream_t s) {
         }
     } pp;
     if (Ltop > 0) {
+        g_allocs.fetch_add(2, std::memory_order_relaxed);
         if (cudaMalloc((void**)&pp.p, (size_t)n * DP * 4) != cudaSuccess ||
             cudaMalloc((void**)&pp.i, (size_t)n * 4) != cudaSuccess) {
             cudaGetLastError();
@@ -706,6 +707,7 @@ extern "C" int dtree_build(const float* pts, int64_t n, int32_t d, const dtree_o
     int rc = DTREE_OK;
     auto alloc = [&](void** p, size_t bytes) {
         if (rc != DTREE_OK) return;
+        dt::g_allocs.fetch_add(1, std::memory_order_relaxed);
         if (cudaMalloc(p, bytes) != cudaSuccess) {
             cudaGetLastError();
             rc = DTREE_ERR_OOM;

@@ -40,6 +40,20 @@ struct dtree {
 namespace dt {
 
 extern std::atomic<int64_t> g_launches;
+extern std::atomic<int64_t> g_allocs;  // device allocations made by the library
+
+// A fixed device range that stands in for the stream-ordered pool (the
+// no-allocation entry point), or null.
+struct ScratchArena {
+    unsigned char* base;
+    size_t bytes;
+};
+
+// dtree_knn's checks and dispatch, with its scratch from the pool (arena
+// null) or from a fixed range.
+int knn_entry(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_idx,
+              float* out_dist, const dtree_opts* o, void* stream, dtree_stats* st,
+              const ScratchArena* arena);
 
 // Status of the last failing CUDA call, mapped to dtree_status.
 int cuda_status(cudaError_t e);
@@ -100,6 +114,7 @@ template <class T>
 inline int scratch(T** p, size_t count, cudaStream_t s) {
     *p = nullptr;
     if (count == 0) return DTREE_OK;
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
     cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), s);
     if (e != cudaSuccess) {
         cudaGetLastError();

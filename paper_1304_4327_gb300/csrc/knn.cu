@@ -304,16 +304,50 @@ struct PhaseTimer {
     }
 };
 
+// Per-call scratch: from the device's stream-ordered pool, or (arena set)
+// carved from a fixed device range with no allocation at all.  In the range,
+// blocks are 256-byte aligned and releasing the most recent block gives its
+// bytes back; other releases keep them until the call ends.
 struct Pool {
+    static constexpr int kMaxBlocks = 64;
     cudaStream_t s;
+    const ScratchArena* arena = nullptr;
+    size_t top = 0;
+    int nblk = 0;
+    size_t blk_from[kMaxBlocks];
+    void* blk_ptr[kMaxBlocks];
     std::vector<void*> ptrs;
+
+    // bytes still free in the range after alignment (0 without a range)
+    size_t left() const {
+        if (!arena) return 0;
+        const size_t off = (top + 255) & ~(size_t)255;
+        return off < arena->bytes ? arena->bytes - off : 0;
+    }
     template <class T>
     int get(T** p, size_t count) {
+        if (arena) {
+            *p = nullptr;
+            if (count == 0) return DTREE_OK;
+            const size_t off = (top + 255) & ~(size_t)255;
+            if (nblk >= kMaxBlocks || off > arena->bytes || count > (arena->bytes - off) / sizeof(T))
+                return DTREE_ERR_TOO_LARGE;
+            *p = reinterpret_cast<T*>(arena->base + off);
+            blk_from[nblk] = top;
+            blk_ptr[nblk] = *p;
+            ++nblk;
+            top = off + count * sizeof(T);
+            return DTREE_OK;
+        }
         int rc = scratch(p, count, s);
         if (rc == DTREE_OK && *p) ptrs.push_back(*p);
         return rc;
     }
     void release(void* p) {
+        if (arena) {
+            if (nblk > 0 && blk_ptr[nblk - 1] == p) top = blk_from[--nblk];
+            return;
+        }
         for (auto& q : ptrs)
             if (q == p) {
                 cudaFreeAsync(q, s);
@@ -335,7 +369,7 @@ struct Pool {
 template <int DP>
 int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* out_idx,
              float* out_dist, int qb_cap, int seed_pts, int prec, int spin, cudaStream_t s,
-             dtree_stats* st) {
+             dtree_stats* st, const ScratchArena* arena) {
     const int64_t launches0 = g_launches.load();
     const int64_t nq = tq->n, m = tr->n;
     const int Lb = std::min<int>(tq->height, level_of_count(nq, qb_cap));
@@ -356,7 +390,9 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
     int Ls = 0;
     while (Ls < hr && (m >> (Ls + 1)) >= seed_pts) ++Ls;
 
-    Pool P{s};
+    Pool P;
+    P.s = s;
+    P.arena = arena;
     int32_t *sl0, *sn, *cand_i, *csr_leaf = nullptr;
     int4* fbq_list;
     float *cand_d, *B1n, *An, *Bn, *csr_dmin = nullptr, *csr_key = nullptr;
@@ -439,14 +475,24 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
     // 3. level-synchronous pruning dual-tree traversal
     const int steps = std::max(1, std::max(Lb, hr));
     int64_t cap = std::max<int64_t>(tr->cap_hint, std::max<int64_t>(1 << 20, (int64_t)nblocks * 256));
+    if (arena) {
+        // a fixed range: the pair buffers take what is left, once (the three
+        // blocks' alignment costs at most 3 x 255 bytes)
+        const size_t per = sizeof(int4) + 2 * sizeof(int2);
+        const size_t room = P.left();
+        cap = room > 1024 ? (int64_t)std::min<size_t>((room - 1024) / per, (size_t)1 << 30) : 0;
+        if (cap < 1) return DTREE_ERR_TOO_LARGE;
+    }
     const int egrid = occupancy_grid((const void*)k_expand<DP>, 256, 0);
     int np = 0;
     for (int attempt = 0;; ++attempt) {
         int2 *F0, *F1;
         int4* outp;
+        // in this order, so that in a fixed range releasing F1 then F0 frees
+        // the frontier for the candidate arrays
+        DT_TRY(P.get(&outp, cap));
         DT_TRY(P.get(&F0, cap));
         DT_TRY(P.get(&F1, cap));
-        DT_TRY(P.get(&outp, cap));
         DT_CHECK(cudaMemsetAsync(bcount, 0, nblocks * sizeof(int), s));
         DT_CHECK(cudaMemsetAsync(ctr + 4, 0, 4 * sizeof(int), s));
         int2 root = make_int2(0, 0);
@@ -468,8 +514,8 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
         int hp = 0;
         DT_CHECK(cudaMemcpyAsync(&hp, ctr + 7, sizeof(int), cudaMemcpyDeviceToHost, s));
         DT_CHECK(cudaStreamSynchronize(s));
-        P.release(F0);
         P.release(F1);
+        P.release(F0);
         if (!hv[0]) {
             np = hp;
             DT_TRY(P.get(&csr_leaf, std::max(np, 1)));
@@ -484,12 +530,13 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
             break;
         }
         P.release(outp);
+        if (arena) return DTREE_ERR_TOO_LARGE;  // the fixed range holds no more pairs
         if (cap >= ((int64_t)1 << 30) || attempt > 8) return DTREE_ERR_OOM;
         cap *= 4;
         // the traversal counters restart with the next attempt
         DT_CHECK(cudaMemsetAsync(dstats, 0, 3 * sizeof(unsigned long long), s));
     }
-    const_cast<dtree_t*>(tr)->cap_hint = cap;
+    if (!arena) const_cast<dtree_t*>(tr)->cap_hint = cap;
     tm.mark();  // 2
 
     // 4. BaseCase over the candidates with the tightening bound, re-rank, output
@@ -535,10 +582,9 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
 
 }  // namespace
 
-}  // namespace dt
-
-extern "C" int dtree_knn(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_idx,
-                         float* out_dist, const dtree_opts* o, void* stream, dtree_stats* st) {
+int knn_entry(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_idx,
+              float* out_dist, const dtree_opts* o, void* stream, dtree_stats* st,
+              const ScratchArena* arena) {
     if (st) memset(st, 0, sizeof(*st));
     if (!ref) return DTREE_ERR_INVALID_ARG;
     const bool mono = query == nullptr || query == ref;
@@ -559,7 +605,11 @@ extern "C" int dtree_knn(const dtree_t* query, const dtree_t* ref, int32_t k, in
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0;
     cudaGetDevice(&dev);
-    dt::prepare_pool(dev);
+    if (arena) {
+        if (ref->device != dev || tq->device != dev) return DTREE_ERR_INVALID_ARG;
+    } else {
+        prepare_pool(dev);
+    }
     if (prec != DTREE_PREC_FP32) {
         // the tensor-core tiles are built for sm_103a (tcgen05)
         int major = 0, minor = 0;
@@ -569,12 +619,19 @@ extern "C" int dtree_knn(const dtree_t* query, const dtree_t* ref, int32_t k, in
     }
     int rc;
     switch (ref->dp) {
-        case 4: rc = dt::knn_impl<4>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st); break;
-        case 8: rc = dt::knn_impl<8>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st); break;
-        case 16: rc = dt::knn_impl<16>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st); break;
-        case 32: rc = dt::knn_impl<32>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st); break;
-        default: rc = dt::knn_impl<64>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st); break;
+        case 4: rc = knn_impl<4>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st, arena); break;
+        case 8: rc = knn_impl<8>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st, arena); break;
+        case 16: rc = knn_impl<16>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st, arena); break;
+        case 32: rc = knn_impl<32>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st, arena); break;
+        default: rc = knn_impl<64>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st, arena); break;
     }
     if (rc != DTREE_OK) cudaStreamSynchronize(s);
     return rc;
+}
+
+}  // namespace dt
+
+extern "C" int dtree_knn(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_idx,
+                         float* out_dist, const dtree_opts* o, void* stream, dtree_stats* st) {
+    return dt::knn_entry(query, ref, k, out_idx, out_dist, o, stream, st, nullptr);
 }

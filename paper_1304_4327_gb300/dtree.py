@@ -71,7 +71,10 @@ def _load() -> ctypes.CDLL:
     lib.dtree_debug_tc_timers.restype = ctypes.c_int
     lib.dtree_launch_count.argtypes = []
     lib.dtree_launch_count.restype = _I64
-    for f in (lib.dtree_build, lib.dtree_knn, lib.dtree_export):
+    lib.dtree_alloc_count.argtypes = []
+    lib.dtree_alloc_count.restype = _I64
+    lib.dtree_knn_noalloc.argtypes = [_P, _P, _I32, _P, _P, ctypes.POINTER(dtree_opts), _P]
+    for f in (lib.dtree_build, lib.dtree_knn, lib.dtree_export, lib.dtree_knn_noalloc):
         f.restype = ctypes.c_int
     return lib
 
@@ -86,6 +89,11 @@ def error_string(status: int) -> str:
 def launch_count() -> int:
     """Kernels launched by the library in this process so far."""
     return int(_lib.dtree_launch_count())
+
+
+def alloc_count() -> int:
+    """Device allocations the library has made in this process so far."""
+    return int(_lib.dtree_alloc_count())
 
 
 def _stream(stream) -> ctypes.c_void_p:
@@ -188,6 +196,29 @@ def dtree_knn(query: Optional[Tree], ref: Tree, k: int, precision: str = "fp32",
     if with_stats:
         return out_idx, out_dist, {f: int(getattr(st, f)) for f in STAT_FIELDS}
     return out_idx, out_dist
+
+
+NOALLOC_MAX_QUERIES = 65536
+
+
+def dtree_knn_noalloc(query: Optional[Tree], ref: Tree, k: int, out_idx: torch.Tensor,
+                      out_dist: torch.Tensor, precision: str = "fp32", query_block: int = 0,
+                      seed_points: int = 0, stream=None) -> None:
+    """dtree_knn with no device allocation: the outputs are the caller's
+    (contiguous int64 / float32 (n_q, k) tensors) and the library's scratch
+    is a fixed static array.  Overlapping calls on one device race."""
+    nq = ref.n if query is None else query.n
+    if out_idx.shape != (nq, k) or out_idx.dtype != torch.int64 or not out_idx.is_contiguous():
+        raise ValueError("out_idx must be a contiguous int64 (n_q, k) tensor")
+    if out_dist.shape != (nq, k) or out_dist.dtype != torch.float32 or not out_dist.is_contiguous():
+        raise ValueError("out_dist must be a contiguous float32 (n_q, k) tensor")
+    o = _opts(precision=PRECISIONS[precision], query_block=query_block, seed_points=seed_points)
+    rc = _lib.dtree_knn_noalloc(None if query is None else query.handle, ref.handle, int(k),
+                                ctypes.c_void_p(out_idx.data_ptr()),
+                                ctypes.c_void_p(out_dist.data_ptr()), ctypes.byref(o),
+                                _stream(stream))
+    if rc != DTREE_OK:
+        raise DTreeError(rc, "dtree_knn_noalloc")
 
 
 def dtree_free(tree: Tree) -> None:
