@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="fp32")
+    p.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="bf16")
     p.add_argument("--leaf", type=int, default=32)
     p.add_argument("--query-block", type=int, default=0)
     p.add_argument("--e2e-steps", type=int, default=3)

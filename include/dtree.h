@@ -56,7 +56,10 @@ typedef enum dtree_precision {
     DTREE_PREC_FP32 = 0,   /* CUDA-core float32 differences and squares */
     DTREE_PREC_TF32 = 1,   /* tensor cores (tcgen05), TF32 inputs, FP32 accumulate
                               (d <= 32; wider points return DTREE_ERR_UNSUPPORTED) */
-    DTREE_PREC_BF16 = 2    /* tensor cores (tcgen05), BF16 inputs, FP32 accumulate */
+    DTREE_PREC_BF16 = 2    /* tensor cores (tcgen05), BF16 inputs, FP32 accumulate; for
+                              d <= 32 each centred coordinate is carried as a hi + lo pair
+                              of BF16 values (three BF16 products per term, operand error
+                              about 2^-16), beyond that as one BF16 value (2^-8) */
 } dtree_precision;
 
 /* Options; zero-initialise and set what you need (0 = default). */
@@ -83,7 +86,8 @@ typedef struct dtree_stats {
     int64_t point_pairs;         /* BaseCase(p_q, p_r) evaluations */
     int64_t rerank_candidates;   /* candidates re-ranked in float64 */
     int64_t fallback_queries;    /* queries whose error band overflowed the candidate list
-                                    and were recomputed exactly in float64 */
+                                    and were recomputed over their own candidate leaves
+                                    (float32 keys, float64 re-rank of the band) */
     int64_t query_blocks;        /* work units */
     int64_t kernel_launches;     /* kernels this call launched */
     /* device time of each phase in nanoseconds, from CUDA events recorded on
@@ -92,7 +96,9 @@ typedef struct dtree_stats {
     int64_t ns_traverse;         /* bounds + dual-tree traversal + candidate lists */
     int64_t ns_basecase;         /* main BaseCase pass (tiles, re-rank, output) */
     int64_t ns_fallback;         /* recomputation of overflowed queries */
-    int64_t reserved[2];
+    int64_t fallback64_queries;  /* of those, queries whose float32 band overflowed as
+                                    well, recomputed with float64 keys throughout */
+    int64_t reserved[1];
 } dtree_stats;
 
 typedef struct dtree dtree_t;
@@ -223,11 +229,13 @@ int dtree_debug_mma(const float* A, const float* B, int32_t K, int32_t precision
                     void* stream);
 
 /*
- * dtree_debug_tc_timers -- diagnostic: while `counters` (device, 32 zeroed
- * uint64, or NULL to stop) is set, the main tensor-core BaseCase pass adds
- * per-role clock64 cycle counts to it (window loading, stage waits, stage
- * filling, conversion, epilogue waits and work, ...).  Process-wide; not
- * thread-safe.  (No counterpart in the paper: a performance probe.)
+ * dtree_debug_tc_timers -- diagnostic: while `counters` (device, 64 zeroed
+ * uint64, or NULL to stop) is set, the tensor-core BaseCase passes add
+ * per-role clock64 cycle counts and event counts to it (window loading,
+ * stage waits, stage filling, conversion, epilogue waits and work, list
+ * insertions, ...): counters 0..31 for the main pass, 32..63 for the seed
+ * pass.  Process-wide; not thread-safe.  (No counterpart in the paper: a
+ * performance probe.)
  */
 int dtree_debug_tc_timers(unsigned long long* counters);
 

@@ -366,6 +366,11 @@ struct Pool {
         if (rc_ != DTREE_OK) return rc_; \
     } while (0)
 
+// Candidate-list lengths come in buckets of 4, 8, 16, 24 and 32.
+inline int kc_bucket(int need) {
+    return need <= 4 ? 4 : need <= 8 ? 8 : need <= 16 ? 16 : need <= 24 ? 24 : 32;
+}
+
 template <int DP>
 int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* out_idx,
              float* out_dist, int qb_cap, int seed_pts, int prec, int spin, cudaStream_t s,
@@ -383,9 +388,10 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
     // tensor-core band is wider, so its lists are longer)
     const int fmt = prec == DTREE_PREC_BF16 ? 1 : prec == DTREE_PREC_TF32 ? 2 : 0;
     // list length: k plus room for the candidates inside the error band
-    // (TF32 band ~1% of d^2 at d=16, BF16 ~5%); buckets 4, 8, 16, 24, 32
-    const int kc_need = fmt == 1 ? 2 * k + 12 : fmt == 2 ? k + 14 : k + 1;
-    int KC = kc_need <= 4 ? 4 : kc_need <= 8 ? 8 : kc_need <= 16 ? 16 : kc_need <= 24 ? 24 : 32;
+    // (TF32 and split BF16 bands ~1% of d^2 at d=16, single BF16 ~5%, used
+    // beyond 32 dimensions); buckets 4, 8, 16, 24, 32
+    const int kc_need = fmt == 1 ? (DP <= 32 ? k + 14 : 2 * k + 12) : fmt == 2 ? k + 14 : k + 1;
+    const int KC = kc_bucket(kc_need);
     if (k + 1 > 32) return DTREE_ERR_UNSUPPORTED;
     int Ls = 0;
     while (Ls < hr && (m >> (Ls + 1)) >= seed_pts) ++Ls;
@@ -394,7 +400,7 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
     P.s = s;
     P.arena = arena;
     int32_t *sl0, *sn, *cand_i, *csr_leaf = nullptr;
-    int4* fbq_list;
+    int4 *fbq_list, *fbq2_list;
     float *cand_d, *B1n, *An, *Bn, *csr_dmin = nullptr, *csr_key = nullptr;
     int *ctr, *bcount, *bcur;
     int64_t* off;
@@ -417,6 +423,7 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
     DT_TRY(P.get(&bcount, nblocks));
     DT_TRY(P.get(&bcur, nblocks));
     DT_TRY(P.get(&fbq_list, nq));
+    DT_TRY(P.get(&fbq2_list, nq));
     DT_TRY(P.get(&off, nblocks + 1));
     DT_TRY(P.get(&dstats, ST_NSTAT));
     DT_CHECK(cudaMemsetAsync(ctr, 0, 16 * sizeof(int), s));
@@ -455,6 +462,8 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
     a.out_dist = out_dist;
     a.fbq_list = fbq_list;
     a.fbq_count = ctr + 3;
+    a.fbq2_list = fbq2_list;
+    a.fbq2_count = ctr + 8;
     a.stats = dstats;
     a.work_ctr = ctr + 0;
     auto tile = [&](int mode, int items) -> int {
@@ -462,7 +471,13 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
             return launch_tile_tc<DP>(a, fmt, KC, mode, items, derr, spin, s);
         return launch_tile_cc<DP>(a, KC, mode, items, s);
     };
-    DT_TRY(tile(MODE_SEED, nblocks * cpb));
+    // the seed pass runs on the CUDA cores whatever the precision: its lists
+    // start empty, so nearly every early candidate is an insertion, which the
+    // float32 tile does cheaply; its keys (relative error <= rel_eps) are
+    // tighter than any tensor-core key, so the main pass's bounds hold for them
+    // with lists of bucket(k + 1) entries (the float32 band needs no more)
+    a.kc_rows = KC;
+    DT_TRY(launch_tile_cc<DP>(a, kc_bucket(k + 1), MODE_SEED, nblocks * cpb, s));
     tm.mark();  // 1
 
     // 2. bounds of every query node down to the blocks
@@ -485,18 +500,85 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
     }
     const int egrid = occupancy_grid((const void*)k_expand<DP>, 256, 0);
     int np = 0;
-    for (int attempt = 0;; ++attempt) {
+    int4* outp = nullptr;
+    auto finish_csr = [&](int npairs) -> int {
+        np = npairs;
+        DT_TRY(P.get(&csr_leaf, std::max(np, 1)));
+        DT_TRY(P.get(&csr_dmin, std::max(np, 1)));
+        DT_TRY(P.get(&csr_key, std::max(np, 1)));
+        DT_LAUNCH(k_scan, 1, 1024, 0, s, bcount, nblocks, off);
+        DT_CHECK(cudaMemsetAsync(bcur, 0, nblocks * sizeof(int), s));
+        if (np > 0)
+            DT_LAUNCH(k_csr_fill, (np + 255) / 256, 256, 0, s, outp, np, off, bcur, csr_leaf,
+                      csr_dmin, csr_key);
+        P.release(outp);
+        return DTREE_OK;
+    };
+    const int2 root = make_int2(0, 0);
+    const int one = 1;
+    if (!arena) {
+        // Buffers sized level by level: a frontier pair has at most four child
+        // pairs, so before each level the output frontier and the candidate
+        // buffer get room for four times the current frontier (the frontier
+        // size is read back after every level).
+        int2* F[2];
+        int64_t fcap[2] = {cap, cap}, ocap = cap;
+        DT_TRY(P.get(&outp, ocap));
+        DT_TRY(P.get(&F[0], fcap[0]));
+        DT_TRY(P.get(&F[1], fcap[1]));
+        DT_CHECK(cudaMemsetAsync(bcount, 0, nblocks * sizeof(int), s));
+        DT_CHECK(cudaMemsetAsync(ctr + 4, 0, 4 * sizeof(int), s));
+        DT_CHECK(cudaMemcpyAsync(F[0], &root, sizeof(int2), cudaMemcpyHostToDevice, s));
+        DT_CHECK(cudaMemcpyAsync(ctr + 5, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+        int* nc[2] = {ctr + 5, ctr + 6};
+        int cur = 0;
+        int64_t nf = 1, used = 0;
+        for (int t = 0; t < steps && nf > 0; ++t) {
+            const int nx = cur ^ 1;
+            const int64_t need = 4 * nf;
+            if (need > ((int64_t)1 << 31) - 1 || used + need > ((int64_t)1 << 31) - 1)
+                return DTREE_ERR_OOM;  // pair counters are 32-bit
+            if (fcap[nx] < need) {
+                P.release(F[nx]);
+                fcap[nx] = std::max(need, 2 * fcap[nx]);
+                DT_TRY(P.get(&F[nx], fcap[nx]));
+            }
+            if (ocap - used < need) {
+                int4* o2;
+                const int64_t oc2 = std::max(used + need, 2 * ocap);
+                DT_TRY(P.get(&o2, oc2));
+                if (used > 0)
+                    DT_CHECK(cudaMemcpyAsync(o2, outp, used * sizeof(int4), cudaMemcpyDeviceToDevice, s));
+                P.release(outp);
+                outp = o2;
+                ocap = oc2;
+            }
+            DT_CHECK(cudaMemsetAsync(nc[nx], 0, sizeof(int), s));
+            DT_TRY(launch_expand<DP>(tq->box, tr->box, Bn, F[cur], nc[cur], F[nx], nc[nx], fcap[nx],
+                                     outp, ctr + 7, ocap, bcount, Lb, hr, qblock0, rleaf0, sl0, sn,
+                                     ctr + 4, dstats, egrid, s));
+            int hv[4];
+            DT_CHECK(cudaMemcpyAsync(hv, ctr + 4, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+            DT_CHECK(cudaStreamSynchronize(s));
+            if (hv[0]) return DTREE_ERR_CUDA;  // cannot happen: the buffers were sized for it
+            nf = hv[1 + nx];
+            used = hv[3];
+            cur = nx;
+        }
+        P.release(F[1]);
+        P.release(F[0]);
+        cap = std::max(fcap[0], std::max(fcap[1], ocap));
+        DT_TRY(finish_csr((int)used));
+    } else {
+        // a fixed range: one pass with the capacity it has left
         int2 *F0, *F1;
-        int4* outp;
-        // in this order, so that in a fixed range releasing F1 then F0 frees
-        // the frontier for the candidate arrays
+        // in this order, so that releasing F1 then F0 frees the frontier for
+        // the candidate arrays
         DT_TRY(P.get(&outp, cap));
         DT_TRY(P.get(&F0, cap));
         DT_TRY(P.get(&F1, cap));
         DT_CHECK(cudaMemsetAsync(bcount, 0, nblocks * sizeof(int), s));
         DT_CHECK(cudaMemsetAsync(ctr + 4, 0, 4 * sizeof(int), s));
-        int2 root = make_int2(0, 0);
-        int one = 1;
         DT_CHECK(cudaMemcpyAsync(F0, &root, sizeof(int2), cudaMemcpyHostToDevice, s));
         DT_CHECK(cudaMemcpyAsync(ctr + 5, &one, sizeof(int), cudaMemcpyHostToDevice, s));
         int2 *fi = F0, *fo = F1;
@@ -509,32 +591,13 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
             std::swap(fi, fo);
             std::swap(ni, no);
         }
-        int hv[2];
-        DT_CHECK(cudaMemcpyAsync(hv, ctr + 4, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-        int hp = 0;
-        DT_CHECK(cudaMemcpyAsync(&hp, ctr + 7, sizeof(int), cudaMemcpyDeviceToHost, s));
+        int hv[4];
+        DT_CHECK(cudaMemcpyAsync(hv, ctr + 4, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
         DT_CHECK(cudaStreamSynchronize(s));
         P.release(F1);
         P.release(F0);
-        if (!hv[0]) {
-            np = hp;
-            DT_TRY(P.get(&csr_leaf, std::max(np, 1)));
-            DT_TRY(P.get(&csr_dmin, std::max(np, 1)));
-            DT_TRY(P.get(&csr_key, std::max(np, 1)));
-            DT_LAUNCH(k_scan, 1, 1024, 0, s, bcount, nblocks, off);
-            DT_CHECK(cudaMemsetAsync(bcur, 0, nblocks * sizeof(int), s));
-            if (np > 0)
-                DT_LAUNCH(k_csr_fill, (np + 255) / 256, 256, 0, s, outp, np, off, bcur, csr_leaf,
-                          csr_dmin, csr_key);
-            P.release(outp);
-            break;
-        }
-        P.release(outp);
-        if (arena) return DTREE_ERR_TOO_LARGE;  // the fixed range holds no more pairs
-        if (cap >= ((int64_t)1 << 30) || attempt > 8) return DTREE_ERR_OOM;
-        cap *= 4;
-        // the traversal counters restart with the next attempt
-        DT_CHECK(cudaMemsetAsync(dstats, 0, 3 * sizeof(unsigned long long), s));
+        if (hv[0]) return DTREE_ERR_TOO_LARGE;  // the fixed range holds no more pairs
+        DT_TRY(finish_csr(hv[3]));
     }
     if (!arena) const_cast<dtree_t*>(tr)->cap_hint = cap;
     tm.mark();  // 2
@@ -554,8 +617,16 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
     DT_CHECK(cudaStreamSynchronize(s));
     if (herr) return DTREE_ERR_TIMEOUT;
 
-    // 5. exact float64 recomputation of the queries whose band overflowed
-    if (nfb > 0) DT_TRY(launch_query_fb<DP>(a, KC, nfb, s));
+    // 5. recomputation of the queries whose band overflowed: float32 keys
+    //    with a float64 re-rank of their band, and exact float64 for those
+    //    whose float32 band overflows too
+    int nfb2 = 0;
+    if (nfb > 0) {
+        DT_TRY(launch_query_fb<DP>(a, KC, nfb, false, s));
+        DT_CHECK(cudaMemcpyAsync(&nfb2, ctr + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
+        DT_CHECK(cudaStreamSynchronize(s));
+        if (nfb2 > 0) DT_TRY(launch_query_fb<DP>(a, KC, nfb2, true, s));
+    }
     tm.mark();  // 4
     unsigned long long hs[ST_NSTAT];
     DT_CHECK(cudaMemcpyAsync(hs, dstats, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -570,6 +641,7 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
         st->point_pairs = (int64_t)hs[ST_POINT_PAIRS];
         st->rerank_candidates = (int64_t)hs[ST_RERANK];
         st->fallback_queries = nfb;
+        st->fallback64_queries = nfb2;
         st->query_blocks = nblocks;
         st->kernel_launches = g_launches.load() - launches0;
         st->ns_seed = tm.ns(0, 1);

@@ -55,7 +55,8 @@ struct TileArgs {
     const float* csr_dmin;
     const float* csr_key;       // evaluation order: distance between block and leaf box centres
     const float* Bq;            // per block: B of the block from the traversal (or null)
-    // approximate candidate lists, [KC][nq] layout
+    // approximate candidate lists, [kc_rows][nq] layout
+    int kc_rows;
     float* cand_d;
     int32_t* cand_i;
     float* qub;                 // per query: upper bound on its true k-th distance (seed pass)
@@ -68,6 +69,8 @@ struct TileArgs {
     float* out_dist;
     int4* fbq_list;    // queries whose error band overflowed: (tree position, block, ub bits, 0)
     int* fbq_count;
+    int4* fbq2_list;   // of those, queries whose float32 band overflowed too
+    int* fbq2_count;
     unsigned long long* stats;
 };
 
@@ -75,7 +78,7 @@ template <int DP>
 int launch_tile_cc(const TileArgs& a, int kc, int mode, int items, cudaStream_t s);
 
 template <int DP>
-int launch_query_fb(const TileArgs& a, int kc, int nfbq, cudaStream_t s);
+int launch_query_fb(const TileArgs& a, int kc, int nfbq, bool exact, cudaStream_t s);
 
 template <int DP>
 int launch_tile_tc(const TileArgs& a, int fmt, int kc, int mode, int items, int* err, int spin,

@@ -30,27 +30,50 @@
 
 namespace dt {
 
+// Operand formats.  hw is the MMA's input type (1 = BF16 with .kind::f16,
+// 2 = TF32 with .kind::tf32); split is how many copies of the d coordinates a
+// row carries; u bounds the relative error of a centred coordinate as the
+// MMA sees it; cross bounds, relative to a^2 + b^2, what the norm columns'
+// hi/lo split and any dropped product add to the key.
 template <int FMT>
 struct TcFmt;
 template <>
 struct TcFmt<1> {  // BF16: 8 significant bits
-    static constexpr int esize = 2, kstep = 16;
+    static constexpr int esize = 2, kstep = 16, hw = 1, split = 1;
     static constexpr float u = 0.00390625f;  // 2^-8
+    static constexpr float cross = u * u;
 };
 template <>
 struct TcFmt<2> {  // TF32 (round to nearest): 11 significant bits
-    static constexpr int esize = 4, kstep = 8;
+    static constexpr int esize = 4, kstep = 8, hw = 2, split = 1;
     static constexpr float u = 0.00048828125f;  // 2^-11
+    static constexpr float cross = u * u;
+};
+// Split BF16: a centred coordinate x is carried as hi = bf16(x) and
+// lo = bf16(x - hi), so |x - (hi + lo)| <= 2^-8 |x - hi| <= 2^-16 |x|; three
+// BF16 products per coordinate (hi.hi + lo.hi + hi.lo) leave out lo.lo, whose
+// size in the key is at most 2 (1 + 2^-8)^2 2^-16 |q||r|.
+template <>
+struct TcFmt<3> {
+    static constexpr int esize = 2, kstep = 16, hw = 1, split = 3;
+    static constexpr float u = 1.5411377e-05f;   // 2^-16 (1 + 2^-8)
+    // 2^-16 (norm split) + 1.01 x 2^-16 (lo.lo, as 2 |q||r| <= a^2 + b^2): 3.1e-5, rounded up
+    static constexpr float cross = 4.6e-05f;
 };
 
-// Operand rows carry DP coordinates plus two augmented columns:
-//   A row (query):     -2 q~_1 .. -2 q~_d, 1, 1
-//   B row (reference):    r~_1 ..    r~_d, hi(|r~|^2), lo(|r~|^2)
+// Operand rows carry the centred coordinates plus two augmented columns:
+//   BF16 / TF32 (split 1)
+//     A row (query):     -2 q~_1 .. -2 q~_d, 1, 1
+//     B row (reference):    r~_1 ..    r~_d, hi(|r~|^2), lo(|r~|^2)
+//   split BF16 (split 3), with q^ = q_hi + q_lo and r^ likewise
+//     A row: -2 q_hi, -2 q_lo, -2 q_hi, 1, 1
+//     B row:    r_hi,    r_hi,    r_lo, hi(|r^|^2), lo(|r^|^2)
 // so the accumulator holds w = |r~|^2 - 2 q~.r~ directly (hi + lo carries the
 // float32 norm to about twice the input precision); K is padded to the MMA step.
 template <int FMT, int DP>
 struct TcShape {
-    static constexpr int KP = (DP + 2 + TcFmt<FMT>::kstep - 1) / TcFmt<FMT>::kstep * TcFmt<FMT>::kstep;
+    static constexpr int KD = DP * TcFmt<FMT>::split;  // coordinate columns
+    static constexpr int KP = (KD + 2 + TcFmt<FMT>::kstep - 1) / TcFmt<FMT>::kstep * TcFmt<FMT>::kstep;
     static constexpr int RB = KP * TcFmt<FMT>::esize;  // bytes per operand row
     static constexpr int NCH = RB / 16;                // 16-byte chunks per row
     static constexpr int SBO = NCH * 128;
@@ -60,7 +83,7 @@ struct TcShape {
     static constexpr int SORTCAP = DP >= 64 ? 512 : 1024;        // candidates per window
     static constexpr int CB = DP >= 32 ? 8 : 16;                 // deferred insertions per thread
     static constexpr int RAWB = TN * DP * 4;                     // raw float32 rows of a stage
-    static constexpr int RINGB = DP >= 32 ? 32768 : 65536;      // raw ring budget
+    static constexpr int RINGB = (DP >= 32 || RB >= 128) ? 32768 : 65536;  // raw ring budget
     static constexpr int NR = RINGB / RAWB > 8 ? 8 : (RINGB / RAWB < 2 ? 2 : RINGB / RAWB);
 };
 
@@ -91,7 +114,7 @@ struct TcBound {
     // accumulation over K terms, the norms and the epilogue add, plus the
     // hi/lo split of |r~|^2 (relative residual u_p^2)
     static constexpr float alpha =
-        ((4.f * TcShape<FMT, DP>::KP + 16.f) * u + TcFmt<FMT>::u * TcFmt<FMT>::u) * 1.01f;
+        ((4.f * TcShape<FMT, DP>::KP + 16.f) * u + TcFmt<FMT>::cross) * 1.01f;
     // upper bound on the true k-th distance of a query with k-th key S
     __device__ static float ub(float S, float a) {
         if (!(S < INFINITY)) return INFINITY;
@@ -110,6 +133,74 @@ struct TcBound {
         return __fmaf_ru(alpha, n2, __fmul_ru(x, x));
     }
 };
+
+// A centred coordinate rounded to the operand type.
+template <int FMT>
+__device__ __forceinline__ float tc_round(float h) {
+    return TcFmt<FMT>::hw == 2 ? tc::to_tf32(h) : __bfloat162float(__float2bfloat16_rn(h));
+}
+
+// Rounds the centred coordinates h[0..DP): xh gets x~ (split 1) or hi (split
+// 3), xl gets lo (split 3); returns the sum of squares of the represented
+// values (x~ or hi + lo, both exact in float32).
+template <int FMT, int DP>
+__device__ __forceinline__ float tc_round_row(const float* h, float* xh, float* xl) {
+    float n = 0.f;
+#pragma unroll
+    for (int j = 0; j < DP; ++j) {
+        const float hi = tc_round<FMT>(h[j]);
+        float r = hi;
+        if (TcFmt<FMT>::split == 3) {
+            const float lo = tc_round<FMT>(h[j] - hi);
+            xl[j] = lo;
+            r = hi + lo;
+        }
+        xh[j] = hi;
+        n = fmaf(r, r, n);
+    }
+    return n;
+}
+
+// Element e of an operand row (A: query, scaled by -2 and ending 1, 1;
+// B: reference, ending with the norm's hi and lo), laid out as above.
+template <int FMT, int DP, bool AROW>
+__device__ __forceinline__ float tc_row_elem(int e, const float* xh, const float* xl, float nhi,
+                                             float nlo) {
+    const float sc = AROW ? -2.f : 1.f;
+    if (TcFmt<FMT>::split == 3) {
+        if (e < DP) return sc * xh[e];
+        if (e < 2 * DP) return sc * (AROW ? xl[e - DP] : xh[e - DP]);
+        if (e < 3 * DP) return sc * (AROW ? xh[e - 2 * DP] : xl[e - 2 * DP]);
+        e -= 2 * DP;
+    } else if (e < DP) {
+        return sc * xh[e];
+    }
+    if (e == DP) return AROW ? 1.f : nhi;
+    if (e == DP + 1) return AROW ? 1.f : nlo;
+    return 0.f;
+}
+
+// The 16 bytes of chunk c of an operand row.
+template <int FMT, int DP, bool AROW>
+__device__ __forceinline__ uint4 tc_row_chunk(int c, const float* xh, const float* xl, float nhi,
+                                              float nlo) {
+    uint4 w;
+    uint32_t* p = reinterpret_cast<uint32_t*>(&w);
+    if (TcFmt<FMT>::esize == 2) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __nv_bfloat162 b = __floats2bfloat162_rn(
+                tc_row_elem<FMT, DP, AROW>(8 * c + 2 * i, xh, xl, nhi, nlo),
+                tc_row_elem<FMT, DP, AROW>(8 * c + 2 * i + 1, xh, xl, nhi, nlo));
+            p[i] = *reinterpret_cast<uint32_t*>(&b);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            p[i] = __float_as_uint(tc_row_elem<FMT, DP, AROW>(4 * c + i, xh, xl, nhi, nlo));
+    }
+    return w;
+}
 
 struct TcExtra {
     int* err;          // device status word: 1 = a bounded wait gave up
@@ -137,6 +228,7 @@ enum TcTimer {
     TT_EPI_FLUSH,        // epilogue (warp 0): the end-of-tile insertion of buffered candidates
     TT_TILES,            // converters: tiles produced
     TT_ITEMS,            // items processed
+    TT_INSERTS,          // epilogue (all threads): candidate-list insertions
     TT_N
 };
 static_assert(TT_N <= 32, "the diagnostic timer buffer holds 32 counters");
@@ -233,7 +325,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
     const int role = warp < 4 ? 0 : warp < 8 ? 1 : warp == 8 ? 2 : 3;
     const int qt = tid & 127;  // query row of an epilogue thread
     const int nitems = a.nwork * a.cpb;
-    unsigned long long n_skip = 0, n_eval = 0, n_pp = 0, n_re = 0;
+    unsigned long long n_skip = 0, n_eval = 0, n_pp = 0, n_re = 0, n_ins = 0;
 
     if (tid == 0) {
         for (int i = 0; i < NS; ++i) {
@@ -252,7 +344,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = s_tmem;
-    const uint32_t idesc = tc::idesc(FMT, kQB, TN);
+    const uint32_t idesc = tc::idesc(TcFmt<FMT>::hw, kQB, TN);
     uint32_t rtile = 0;     // planner / converters: next raw stage
     uint32_t ptile = 0;     // converters: next operand slot use
     uint32_t ctile = role;  // epilogue group: next operand slot use of this group
@@ -284,45 +376,27 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
         if (role < 2) {
             // the query, centred and rounded (group 0 writes row qt of the A tile)
             float qa2 = 0.f;
-            float hv[S::KP];
+            float h[DP], xh[DP], xl[DP];
             const float4* q4 = reinterpret_cast<const float4*>(a.qpts + (int64_t)myq * DP);
 #pragma unroll
             for (int j = 0; j < DP / 4; ++j) {
                 float4 v = act ? q4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-                hv[4 * j] = v.x;
-                hv[4 * j + 1] = v.y;
-                hv[4 * j + 2] = v.z;
-                hv[4 * j + 3] = v.w;
+                h[4 * j] = v.x;
+                h[4 * j + 1] = v.y;
+                h[4 * j + 2] = v.z;
+                h[4 * j + 3] = v.w;
             }
 #pragma unroll
-            for (int j = 0; j < S::KP; ++j) {
-                float h = (j < DP && act) ? hv[j] - scen[j] : 0.f;
-                qa2 = __fmaf_ru(h, h, qa2);
-                float r = FMT == 1 ? __bfloat162float(__float2bfloat16_rn(h)) : tc::to_tf32(h);
-                qn = fmaf(r, r, qn);
-                hv[j] = j < DP ? -2.f * r : (j < DP + 2 ? 1.f : 0.f);
+            for (int j = 0; j < DP; ++j) {
+                h[j] = act ? h[j] - scen[j] : 0.f;
+                qa2 = __fmaf_ru(h[j], h[j], qa2);
             }
+            qn = tc_round_row<FMT, DP>(h, xh, xl);
             if (role == 0) {
 #pragma unroll
-                for (int c = 0; c < S::NCH; ++c) {
-                    uint4 w;
-                    if (FMT == 1) {
-                        __nv_bfloat162 p0 = __floats2bfloat162_rn(hv[8 * c], hv[8 * c + 1]);
-                        __nv_bfloat162 p1 = __floats2bfloat162_rn(hv[8 * c + 2], hv[8 * c + 3]);
-                        __nv_bfloat162 p2 = __floats2bfloat162_rn(hv[8 * c + 4], hv[8 * c + 5]);
-                        __nv_bfloat162 p3 = __floats2bfloat162_rn(hv[8 * c + 6], hv[8 * c + 7]);
-                        w.x = *reinterpret_cast<uint32_t*>(&p0);
-                        w.y = *reinterpret_cast<uint32_t*>(&p1);
-                        w.z = *reinterpret_cast<uint32_t*>(&p2);
-                        w.w = *reinterpret_cast<uint32_t*>(&p3);
-                    } else {
-                        w.x = __float_as_uint(hv[4 * c]);
-                        w.y = __float_as_uint(hv[4 * c + 1]);
-                        w.z = __float_as_uint(hv[4 * c + 2]);
-                        w.w = __float_as_uint(hv[4 * c + 3]);
-                    }
-                    *reinterpret_cast<uint4*>(sA + tc::core_offset(qt, c, S::SBO)) = w;
-                }
+                for (int c = 0; c < S::NCH; ++c)
+                    *reinterpret_cast<uint4*>(sA + tc::core_offset(qt, c, S::SBO)) =
+                        tc_row_chunk<FMT, DP, true>(c, xh, xl, 1.f, 1.f);
             }
             qa = __fsqrt_ru(qa2);
 #pragma unroll
@@ -544,60 +618,32 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                 for (int row = ctid; row < TN; row += 96) {
                     if (row < m) {
                         const float4* r4 = reinterpret_cast<const float4*>(raw + row * DP);
-                        float hv[S::KP];
-                        float rn = 0.f;
+                        float h[DP], xh[DP], xl[DP];
 #pragma unroll
                         for (int j4 = 0; j4 < DP / 4; ++j4) {
                             float4 v = r4[j4];
-                            hv[4 * j4] = v.x;
-                            hv[4 * j4 + 1] = v.y;
-                            hv[4 * j4 + 2] = v.z;
-                            hv[4 * j4 + 3] = v.w;
+                            h[4 * j4] = v.x - scen[4 * j4];
+                            h[4 * j4 + 1] = v.y - scen[4 * j4 + 1];
+                            h[4 * j4 + 2] = v.z - scen[4 * j4 + 2];
+                            h[4 * j4 + 3] = v.w - scen[4 * j4 + 3];
                         }
+                        const float rn = tc_round_row<FMT, DP>(h, xh, xl);
+                        const float nhi = tc_round<FMT>(rn);
+                        const float nlo = tc_round<FMT>(rn - nhi);
 #pragma unroll
-                        for (int j = 0; j < DP; ++j) {
-                            float h = hv[j] - scen[j];
-                            float rr = FMT == 1 ? __bfloat162float(__float2bfloat16_rn(h)) : tc::to_tf32(h);
-                            hv[j] = rr;
-                            rn = fmaf(rr, rr, rn);
-                        }
-                        {
-                            float hi = FMT == 1 ? __bfloat162float(__float2bfloat16_rn(rn)) : tc::to_tf32(rn);
-                            float lo = rn - hi;
-                            lo = FMT == 1 ? __bfloat162float(__float2bfloat16_rn(lo)) : tc::to_tf32(lo);
-#pragma unroll
-                            for (int j = DP; j < S::KP; ++j) hv[j] = j == DP ? hi : (j == DP + 1 ? lo : 0.f);
-                        }
-#pragma unroll
-                        for (int c = 0; c < S::NCH; ++c) {
-                            uint4 w;
-                            if (FMT == 1) {
-                                __nv_bfloat162 p0 = __floats2bfloat162_rn(hv[8 * c], hv[8 * c + 1]);
-                                __nv_bfloat162 p1 = __floats2bfloat162_rn(hv[8 * c + 2], hv[8 * c + 3]);
-                                __nv_bfloat162 p2 = __floats2bfloat162_rn(hv[8 * c + 4], hv[8 * c + 5]);
-                                __nv_bfloat162 p3 = __floats2bfloat162_rn(hv[8 * c + 6], hv[8 * c + 7]);
-                                w.x = *reinterpret_cast<uint32_t*>(&p0);
-                                w.y = *reinterpret_cast<uint32_t*>(&p1);
-                                w.z = *reinterpret_cast<uint32_t*>(&p2);
-                                w.w = *reinterpret_cast<uint32_t*>(&p3);
-                            } else {
-                                w.x = __float_as_uint(hv[4 * c]);
-                                w.y = __float_as_uint(hv[4 * c + 1]);
-                                w.z = __float_as_uint(hv[4 * c + 2]);
-                                w.w = __float_as_uint(hv[4 * c + 3]);
-                            }
-                            *reinterpret_cast<uint4*>(sBs + tc::core_offset(row, c, S::SBO)) = w;
-                        }
+                        for (int c = 0; c < S::NCH; ++c)
+                            *reinterpret_cast<uint4*>(sBs + tc::core_offset(row, c, S::SBO)) =
+                                tc_row_chunk<FMT, DP, false>(c, xh, xl, nhi, nlo);
                         sposs[row] = rpos[row];
                     } else {
                         // an empty column: w = +inf never qualifies
 #pragma unroll
                         for (int c = 0; c < S::NCH; ++c) {
                             uint4 w = make_uint4(0u, 0u, 0u, 0u);
-                            const int el = (DP * TcFmt<FMT>::esize) / 16 == c ? DP % (16 / TcFmt<FMT>::esize) : -1;
+                            const int el = (S::KD * TcFmt<FMT>::esize) / 16 == c ? S::KD % (16 / TcFmt<FMT>::esize) : -1;
                             if (el >= 0) {
                                 // place +inf in the hi(|r~|^2) element of this chunk
-                                if (FMT == 1) {
+                                if (TcFmt<FMT>::esize == 2) {
                                     uint32_t inf16 = 0x7f80u;
                                     uint32_t* wp = reinterpret_cast<uint32_t*>(&w);
                                     wp[el >> 1] = (el & 1) ? (inf16 << 16) : inf16;
@@ -621,7 +667,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                     const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sBs);
 #pragma unroll
                     for (int kk = 0; kk < S::NK; ++kk)
-                        tc::mma<FMT>(tmem + (uint32_t)(slot * TN),
+                        tc::mma<TcFmt<FMT>::hw>(tmem + (uint32_t)(slot * TN),
                                      tc::sdesc(a0 + 256u * kk, 128u, S::SBO),
                                      tc::sdesc(b0 + 256u * kk, 128u, S::SBO), idesc, kk > 0 ? 1u : 0u);
                     tc::mma_commit(&full[slot]);
@@ -682,6 +728,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                                 list_insert_par(ld, li, sv, rp);
                                 t = kth_moves ? threshold() : fminf(t, __fsub_ru(ld[KC - 1], qn));
                                 changed = true;
+                                ++n_ins;
                             }
                         }
                         nb = 0;
@@ -863,6 +910,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
     if (n_eval) atomicAdd(&a.stats[ST_EVALUATED], n_eval);
     if (n_pp) atomicAdd(&a.stats[ST_POINT_PAIRS], n_pp);
     if (n_re) atomicAdd(&a.stats[ST_RERANK], n_re);
+    if (x.timers && n_ins) atomicAdd(&x.timers[TT_INSERTS], n_ins);
 }
 
 // The kernel allocates all 512 TMEM columns, so at most one CTA may be
@@ -884,15 +932,20 @@ extern unsigned long long* g_tc_timers;
 template <int DP>
 int launch_tile_tc(const TileArgs& a, int fmt, int kc, int mode, int items, int* err, int spin,
                    cudaStream_t s) {
-    TcExtra x{err, spin, mode == MODE_MAIN ? g_tc_timers : nullptr};
+    // counters 0..31 for the main pass, 32..63 for the seed pass
+    // the seed pass runs on the CUDA cores (launch_tile_cc)
+    if (mode != MODE_MAIN) return DTREE_ERR_UNSUPPORTED;
+    TcExtra x{err, spin, g_tc_timers};
     // TF32 operand rows of 64 dimensions do not fit the pipeline's shared
     // memory; BF16 serves that width (where the MMA cost matters most)
     if (DP > 32 && fmt == 2) return DTREE_ERR_UNSUPPORTED;
+    // BF16 requests: split BF16 (hi + lo per coordinate) up to 32 dimensions,
+    // single BF16 beyond (whose operand rows would not fit shared memory split)
+    if (fmt == 1 && DP <= 32) fmt = 3;
 #define DT_TC_CASE(FMTV, KCV)                                                              \
-    if constexpr (!(DP > 32 && FMTV == 2))                                                 \
+    if constexpr (!(DP > 32 && FMTV != 1) && !(DP <= 32 && FMTV == 1))                     \
     if (fmt == FMTV && kc == KCV) {                                                        \
-        auto kern = mode == MODE_SEED ? k_tile_tc<FMTV, DP, KCV, MODE_SEED>                \
-                                      : k_tile_tc<FMTV, DP, KCV, MODE_MAIN>;               \
+        auto kern = k_tile_tc<FMTV, DP, KCV, MODE_MAIN>;                                   \
         size_t smem = tc_smem_bytes<FMTV, DP, KCV>();                                      \
         DT_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                       (int)smem));                                         \
@@ -911,6 +964,11 @@ int launch_tile_tc(const TileArgs& a, int fmt, int kc, int mode, int items, int*
     DT_TC_CASE(2, 16)
     DT_TC_CASE(2, 24)
     DT_TC_CASE(2, 32)
+    DT_TC_CASE(3, 4)
+    DT_TC_CASE(3, 8)
+    DT_TC_CASE(3, 16)
+    DT_TC_CASE(3, 24)
+    DT_TC_CASE(3, 32)
 #undef DT_TC_CASE
     return DTREE_ERR_UNSUPPORTED;
 }

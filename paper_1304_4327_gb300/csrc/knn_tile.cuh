@@ -21,6 +21,8 @@
 // recomputed in float64 (k_query_fb), where keys are exact.
 #pragma once
 
+#include <type_traits>
+
 #include "knn_common.cuh"
 
 namespace dt {
@@ -382,6 +384,11 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
                         a.cand_d[(int64_t)j * a.nq + myq] = (float)ld[j];
                         a.cand_i[(int64_t)j * a.nq + myq] = li[j];
                     }
+                    // the main pass may keep longer lists: their other rows start empty
+                    for (int j = KC; j < a.kc_rows; ++j) {
+                        a.cand_d[(int64_t)j * a.nq + myq] = INFINITY;
+                        a.cand_i[(int64_t)j * a.nq + myq] = kEmptyIdx;
+                    }
                     a.qub[myq] = ub_of<T, DP>(list_at(ld, a.k - 1));
                 }
             } else {
@@ -435,15 +442,19 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
     if (n_re) atomicAdd(&a.stats[ST_RERANK], n_re);
 }
 
-// Exact recomputation of one query whose error band overflowed its list, one
-// CTA per query.  The candidate leaves are its block's seed leaves and
-// traversal candidates; each is kept only if the distance from the query to
-// the leaf's box (rounded down) does not exceed the query's upper bound on its
-// k-th distance (the single-tree form of Algorithm 3's Score), so the work
-// follows the query's own ball, not its block's.  Kept leaves gather in a
-// shared buffer; when it fills, the 128 threads evaluate its points, one
-// point each in turn, in exact float64, each keeping a (distance, index)
-// list; thread 0 merges the 128 sorted lists.
+// Recomputation of one query whose error band overflowed its list, one CTA
+// per query.  The candidate leaves are its block's seed leaves and traversal
+// candidates; each is kept only if the distance from the query to the leaf's
+// box (rounded down) does not exceed the query's upper bound on its k-th
+// distance (the single-tree form of Algorithm 3's Score), so the work follows
+// the query's own ball, not its block's.  Kept leaves gather in a shared
+// buffer; when it fills, the 128 threads evaluate its points, one point each
+// in turn, each keeping a candidate list, and the lists are merged.
+//   EXACT = false  float32 keys (relative error <= rel_eps): the merged KC
+//                  best keys give a band of possible k-th neighbours; if the
+//                  band fits the list, its members are re-ranked in float64
+//                  and written, else the query goes on to the exact pass.
+//   EXACT = true   float64 (distance, index) keys, the result itself.
 constexpr int kFbLeafBuf = 512;
 
 template <int DP>
@@ -457,14 +468,36 @@ __device__ __forceinline__ float point_box_dmin_down(const float* q, const float
     return __fmul_rd(__fsqrt_rd(s), 1.f - rel_eps<DP>());
 }
 
-template <int DP, int KC>
+template <int DP>
+__device__ __forceinline__ float approx_d2(const float* q, const float* r) {
+    const float4* r4 = reinterpret_cast<const float4*>(r);
+    float f = 0.f;
+#pragma unroll
+    for (int j = 0; j < DP / 4; ++j) {
+        const float4 v = r4[j];
+        const float t0 = q[4 * j] - v.x, t1 = q[4 * j + 1] - v.y;
+        const float t2 = q[4 * j + 2] - v.z, t3 = q[4 * j + 3] - v.w;
+        f = fmaf(t0, t0, f);
+        f = fmaf(t1, t1, f);
+        f = fmaf(t2, t2, f);
+        f = fmaf(t3, t3, f);
+    }
+    return f;
+}
+
+template <int DP, int KC, bool EXACT>
 __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
+    using T = typename std::conditional<EXACT, double, float>::type;
     extern __shared__ __align__(16) unsigned char fsm[];
-    double* md = reinterpret_cast<double*>(fsm);                 // KC x 128
+    T* md = reinterpret_cast<T*>(fsm);                           // KC x 128
     int32_t* mi = reinterpret_cast<int32_t*>(md + KC * kQB);     // KC x 128
     __shared__ int s_lb[kFbLeafBuf], s_pre[kFbLeafBuf + 1];
-    __shared__ int s_n;
-    const int4 e = a.fbq_list[blockIdx.x];
+    __shared__ int s_n, s_nb;
+    __shared__ float s_fd[KC];
+    __shared__ int s_fi[KC];
+    __shared__ double s_rd[KC];
+    __shared__ int s_ri[KC];
+    const int4 e = (EXACT ? a.fbq2_list : a.fbq_list)[blockIdx.x];
     const int myq = e.x, blk = e.y;
     const float ub = __int_as_float(e.z);
     const int tid = threadIdx.x;
@@ -480,11 +513,11 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
             q[4 * j + 3] = v.w;
         }
     }
-    double ld[KC];
+    T ld[KC];
     int li[KC];
 #pragma unroll
     for (int j = 0; j < KC; ++j) {
-        ld[j] = (double)INFINITY;
+        ld[j] = (T)INFINITY;
         li[j] = kEmptyIdx;
     }
     const int nseed = a.seed_nleaf[blk], sleaf0 = a.seed_leaf0[blk];
@@ -531,9 +564,14 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
                 }
                 const int r = a.rbeg[a.rleaf0 + s_lb[lo]] + (p - s_pre[lo]);
                 if (a.mono && r == myq) continue;
-                const double d2 = exact_d2<DP>(q, a.rpts + (int64_t)r * DP);
-                const int orig = a.ridx[r];
-                if (key_less(d2, orig, ld[KC - 1], li[KC - 1])) list_insert(ld, li, d2, orig);
+                if constexpr (EXACT) {
+                    const double d2 = exact_d2<DP>(q, a.rpts + (int64_t)r * DP);
+                    const int orig = a.ridx[r];
+                    if (key_less(d2, orig, ld[KC - 1], li[KC - 1])) list_insert(ld, li, d2, orig);
+                } else {
+                    const float d2 = approx_d2<DP>(q, a.rpts + (int64_t)r * DP);
+                    if (key_less(d2, r, ld[KC - 1], li[KC - 1])) list_insert(ld, li, d2, r);
+                }
             }
             __syncthreads();
             if (tid == 0) s_n = 0;
@@ -546,17 +584,19 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
         mi[j * kQB + tid] = li[j];
     }
     __syncthreads();
+    const int64_t obase = (int64_t)a.qidx[myq] * a.k;
+    const int nout = EXACT ? a.k : KC;
     if (tid == 0) {
+        // merge the 128 sorted lists: the first nout keys overall
         int head[kQB];
         for (int t = 0; t < kQB; ++t) head[t] = 0;
-        const int64_t base = (int64_t)a.qidx[myq] * a.k;
-        for (int j = 0; j < a.k; ++j) {
+        for (int j = 0; j < nout; ++j) {
             int best = -1;
-            double bd = (double)INFINITY;
+            T bd = (T)INFINITY;
             int bi = kEmptyIdx;
             for (int t = 0; t < kQB; ++t) {
                 if (head[t] >= KC) continue;
-                const double d = md[head[t] * kQB + t];
+                const T d = md[head[t] * kQB + t];
                 const int i = mi[head[t] * kQB + t];
                 if (best < 0 || key_less(d, i, bd, bi)) {
                     best = t;
@@ -565,20 +605,63 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
                 }
             }
             head[best]++;
-            a.out_idx[base + j] = bi;
-            a.out_dist[base + j] = (float)sqrt(bd);
+            if constexpr (EXACT) {
+                a.out_idx[obase + j] = bi;
+                a.out_dist[obase + j] = (float)sqrt(bd);
+            } else {
+                s_fd[j] = bd;
+                s_fi[j] = bi;
+            }
         }
+        if constexpr (!EXACT) {
+            // every true k-nearest neighbour has a key <= band; the band must
+            // end inside the list, else the float64 pass takes the query
+            const float band = __fmul_ru(s_fd[a.k - 1], 1.f + 4.f * rel_eps<DP>());
+            int n = 0;
+            while (n < KC && s_fi[n] != kEmptyIdx && !(s_fd[n] > band)) ++n;
+            if (n == KC) {
+                a.fbq2_list[atomicAdd(a.fbq2_count, 1)] = e;
+                n = -1;
+            }
+            s_nb = n;
+        }
+    }
+    if constexpr (!EXACT) {
+        __syncthreads();
+        const int n = s_nb;
+        if (n < 0) return;  // uniform: the float64 pass recomputes this query
+        if (tid < n) {
+            s_rd[tid] = exact_d2<DP>(q, a.rpts + (int64_t)s_fi[tid] * DP);
+            s_ri[tid] = a.ridx[s_fi[tid]];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double rd[KC];
+            int ri[KC];
+#pragma unroll
+            for (int j = 0; j < KC; ++j) {
+                rd[j] = (double)INFINITY;
+                ri[j] = kEmptyIdx;
+            }
+            for (int j = 0; j < n; ++j) list_insert(rd, ri, s_rd[j], s_ri[j]);
+            for (int j = 0; j < a.k; ++j) {
+                a.out_idx[obase + j] = ri[j];
+                a.out_dist[obase + j] = (float)sqrt(rd[j]);
+            }
+        }
+        if (tid == 0) atomicAdd(&a.stats[ST_RERANK], (unsigned long long)n);
     }
 }
 
 template <int DP>
-int launch_query_fb(const TileArgs& a, int kc, int nfbq, cudaStream_t s) {
+int launch_query_fb(const TileArgs& a, int kc, int nfbq, bool exact, cudaStream_t s) {
 #define DT_FB_CASE(KCV)                                                                       \
     case KCV: {                                                                               \
-        const size_t smem = (size_t)KCV * kQB * 12;                                           \
-        DT_CHECK(cudaFuncSetAttribute(k_query_fb<DP, KCV>,                                    \
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        DT_LAUNCH((k_query_fb<DP, KCV>), nfbq, kQB, smem, s, a);                              \
+        auto kern = exact ? k_query_fb<DP, KCV, true> : k_query_fb<DP, KCV, false>;           \
+        const size_t smem = (size_t)KCV * kQB * ((exact ? 8 : 4) + 4);                      \
+        DT_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                      (int)smem));                                            \
+        DT_LAUNCH(kern, nfbq, kQB, smem, s, a);                                               \
         return DTREE_OK;                                                                      \
     }
     switch (kc) {

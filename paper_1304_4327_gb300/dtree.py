@@ -30,11 +30,11 @@ class dtree_opts(ctypes.Structure):
 STAT_FIELDS = ("node_pairs_scored", "node_pairs_pruned", "leaf_pairs_emitted",
                "leaf_pairs_skipped", "leaf_pairs_evaluated", "point_pairs",
                "rerank_candidates", "fallback_queries", "query_blocks", "kernel_launches",
-               "ns_seed", "ns_traverse", "ns_basecase", "ns_fallback")
+               "ns_seed", "ns_traverse", "ns_basecase", "ns_fallback", "fallback64_queries")
 
 
 class dtree_stats(ctypes.Structure):
-    _fields_ = [(f, _I64) for f in STAT_FIELDS] + [("reserved", _I64 * 2)]
+    _fields_ = [(f, _I64) for f in STAT_FIELDS] + [("reserved", _I64 * 1)]
 
 
 class DTreeError(RuntimeError):
@@ -269,11 +269,13 @@ def dtree_debug_mma(A: torch.Tensor, B: torch.Tensor, fmt: str = "bf16", stream=
 
 TC_TIMERS = ("plan_window", "plan_wait", "plan_stage", "conv_wait_raw", "conv_wait_slot",
              "conv_work", "epi_wait", "epi_work", "epi_rare_chunks", "epi_finish", "item_setup",
-             "epi_tmem", "epi_hot", "epi_rare_cycles", "epi_tail", "epi_flush", "tiles", "items")
+             "epi_tmem", "epi_hot", "epi_rare_cycles", "epi_tail", "epi_flush", "tiles", "items",
+             "inserts")
 
 
 def dtree_debug_tc_timers(buf: Optional[torch.Tensor]) -> None:
-    """Attach (or with None detach) a zeroed int64 CUDA tensor of 32 counters."""
-    if buf is not None and (buf.numel() < 32 or buf.dtype != torch.int64 or not buf.is_cuda):
-        raise ValueError("the timer buffer must be a CUDA int64 tensor of at least 32 entries")
+    """Attach (or with None detach) a zeroed int64 CUDA tensor of 64 counters:
+    0..31 for the main tensor-core pass, 32..63 for the seed pass."""
+    if buf is not None and (buf.numel() < 64 or buf.dtype != torch.int64 or not buf.is_cuda):
+        raise ValueError("the timer buffer must be a CUDA int64 tensor of at least 64 entries")
     _lib.dtree_debug_tc_timers(None if buf is None else ctypes.c_void_p(buf.data_ptr()))

@@ -127,7 +127,9 @@ def test_duplicates_take_the_float64_path(dt):
     idx, dist, st = run(dt, R, Q, 10, 16, stats=True)
     ti, td = truth(R, Q, 10)
     compare(idx, dist, ti, td, 10)
-    assert st["fallback_queries"] > 0
+    # 7 distinct points: every k-th distance is an exact tie shared by many
+    # points, so the float32 band overflows as well and float64 decides
+    assert st["fallback_queries"] > 0 and st["fallback64_queries"] > 0
     idx, dist, st = run(dt, R, None, 10, 16, stats=True)
     ti, td = truth(R, None, 10)
     compare(idx, dist, ti, td, 10)

@@ -67,9 +67,9 @@ def test_tc_gmm16_scaled(dt, prec):
     ti, td = truth(W.ref, W.query, W.k)
     r = compare(idx, dist, ti, td, W.k)
     assert r["exact"] + r["exempt"] == 20_000
-    # the band overflows for few queries (more in BF16, whose unit roundoff is
-    # 2^-8); those are recomputed exactly, so this bounds cost, not correctness
-    assert st["fallback_queries"] <= (20 if prec == "tf32" else 2000)
+    # the band overflows for few queries (d = 16: TF32, and BF16 as hi + lo
+    # pairs); those are recomputed exactly, so this bounds cost, not correctness
+    assert st["fallback_queries"] <= 20
 
 
 @pytest.mark.parametrize("prec", ["bf16", "tf32"])
