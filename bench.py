@@ -174,14 +174,21 @@ def run_reference(args, rank, world):
 # roofline of the BaseCase tile kernel
 # ---------------------------------------------------------------------------
 
-# DRAM bytes (read + write) of one tile-kernel launch pair (seed + main) per
-# evaluated point pair, from an ncu capture of the 400,000 x 100,000 case of
-# the same workload, scaled to a full launch by the point pairs it evaluates.
-# None until a capture of the current kernel exists.
-TRAFFIC_PER_PAIR = {"fp32": None, "tf32": None, "bf16": None}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one main
+# BaseCase launch, from a one-pass ncu capture of that launch on this
+# workload (4M x 1M, d = 16, k = 10), with the point pairs the launch
+# evaluated; a run's traffic is scaled by its own point pairs (the workload is
+# deterministic, so the ratio is 1 for the default run).  None where no capture
+# of the current kernel exists.
+TRAFFIC_CAPTURE = {"bf16": (3028252672, 129304518243)}
 
 
-def roofline(precision, d, pairs, ns_tile, sms):
+def traffic_of(precision, pairs):
+    cap = TRAFFIC_CAPTURE.get(precision)
+    return None if cap is None else cap[0] * pairs / cap[1]
+
+
+def roofline(precision, d, pairs, ns_tile, sms, captured_workload=True):
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -191,18 +198,17 @@ def roofline(precision, d, pairs, ns_tile, sms):
         src = "of fallback"
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     secs = ns_tile * 1e-9
-    tpp = TRAFFIC_PER_PAIR.get(precision)
-    traffic = tpp * pairs if tpp is not None else None
+    traffic = traffic_of(precision, pairs) if captured_workload else None
     if precision == "fp32":
         flops = 3.0 * d * pairs                  # d subtractions + d FMAs (2 flops each)
         peak = 2.0 * 128 * sms * sm_max * 1e6 / 1e12
-        bound, kernel = "alu", "k_tile (BaseCase, CUDA-core float32)"
+        bound, kernel = "alu", "k_tile main launch (BaseCase, CUDA-core float32)"
         psrc = f"2 x 128 FP32 lanes x {sms} SMs x {sm_max:.0f} MHz"
     else:
         flops = 2.0 * d * pairs                  # one multiply-add per coordinate and pair
         bf16 = float(peaks.get("bf16_tflops_sustained", 1700.0))
         peak = bf16 if precision == "bf16" else bf16 * 1.1 / 2.25
-        bound, kernel = "tensor", f"k_tile_tc (BaseCase, tcgen05 {precision})"
+        bound, kernel = "tensor", f"k_tile_tc main launch (BaseCase, tcgen05 {precision})"
         psrc = (f"measured sustained BF16 dense {bf16:.1f} TFLOP/s ({src})"
                 + ("" if precision == "bf16" else " x 1.1/2.25 (nominal TF32:BF16)"))
     achieved = flops / secs / 1e12 if secs > 0 else 0.0
@@ -324,14 +330,16 @@ def main():
     e2e_ms = max_over_ranks(f0.elapsed_time(f1) / args.e2e_steps, world, "cuda")
     e2e_value = job_rate(world, nq, e2e_ms)
 
-    # roofline of the dominant kernel: the BaseCase tile kernel (its seed and
-    # main launches), timed per call with CUDA events on the launching stream
-    ns_tile = sum(s["ns_seed"] + s["ns_basecase"] for s in stats) / len(stats)
+    # roofline of the dominant kernel: the main BaseCase tile launch, timed per
+    # call with CUDA events on the launching stream
+    ns_tile = sum(s["ns_basecase"] for s in stats) / len(stats)
+    ns_seed = sum(s["ns_seed"] for s in stats) / len(stats)
     ns_fb = sum(s["ns_fallback"] for s in stats) / len(stats)
     ns_trav = sum(s["ns_traverse"] for s in stats) / len(stats)
     pairs = sum(s["point_pairs"] for s in stats) / len(stats)
     sms = props.multi_processor_count
-    roof = roofline(args.precision, d, pairs, ns_tile, sms)
+    roof = roofline(args.precision, d, pairs, ns_tile, sms,
+                    (args.n_ref, args.n_query, args.leaf) == (4_000_000, 1_000_000, 32))
     s0 = stats[-1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -344,13 +352,14 @@ def main():
                    "l2": "inputs (320 MB) larger than the 129 MB L2; no flush",
                    "parallelism": f"{world} GPU(s), one query shard each, reference replicated"},
         "roofline": roof,
-        "phases_ms": {"basecase_tiles": ns_tile / 1e6, "fallback": ns_fb / 1e6,
-                      "traverse": ns_trav / 1e6,
-                      "build_and_rest": ms_max - (ns_tile + ns_fb + ns_trav) / 1e6},
+        "phases_ms": {"seed": ns_seed / 1e6, "basecase_main": ns_tile / 1e6,
+                      "fallback": ns_fb / 1e6, "traverse": ns_trav / 1e6,
+                      "build_and_rest": ms_max - (ns_seed + ns_tile + ns_fb + ns_trav) / 1e6},
         "counters": {k2: s0[k2] for k2 in ("node_pairs_scored", "node_pairs_pruned",
                                           "leaf_pairs_emitted", "leaf_pairs_skipped",
                                           "leaf_pairs_evaluated", "point_pairs",
-                                          "rerank_candidates", "fallback_queries")},
+                                          "rerank_candidates", "fallback_queries",
+                                          "seed_point_pairs")},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(W.ref.nbytes + W.query.nbytes),
                 "d2h_bytes_per_step": int(nq * k * (8 + 4))},

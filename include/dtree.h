@@ -83,7 +83,7 @@ typedef struct dtree_stats {
     int64_t leaf_pairs_emitted;  /* (query block, reference leaf) pairs that survived */
     int64_t leaf_pairs_skipped;  /* emitted pairs pruned later by the tightened B */
     int64_t leaf_pairs_evaluated;/* pairs whose BaseCase tile ran (seed pairs included) */
-    int64_t point_pairs;         /* BaseCase(p_q, p_r) evaluations */
+    int64_t point_pairs;         /* BaseCase(p_q, p_r) evaluations of the main pass */
     int64_t rerank_candidates;   /* candidates re-ranked in float64 */
     int64_t fallback_queries;    /* queries whose error band overflowed the candidate list
                                     and were recomputed over their own candidate leaves
@@ -98,7 +98,7 @@ typedef struct dtree_stats {
     int64_t ns_fallback;         /* recomputation of overflowed queries */
     int64_t fallback64_queries;  /* of those, queries whose float32 band overflowed as
                                     well, recomputed with float64 keys throughout */
-    int64_t reserved[1];
+    int64_t seed_point_pairs;    /* point pairs the seed pass evaluated (not in point_pairs) */
 } dtree_stats;
 
 typedef struct dtree dtree_t;

@@ -639,6 +639,7 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
         st->leaf_pairs_skipped = (int64_t)hs[ST_SKIPPED];
         st->leaf_pairs_evaluated = (int64_t)hs[ST_EVALUATED];
         st->point_pairs = (int64_t)hs[ST_POINT_PAIRS];
+        st->seed_point_pairs = (int64_t)hs[ST_SEED_PAIRS];
         st->rerank_candidates = (int64_t)hs[ST_RERANK];
         st->fallback_queries = nfb;
         st->fallback64_queries = nfb2;

@@ -15,6 +15,7 @@ enum StatSlot {
     ST_POINT_PAIRS,
     ST_RERANK,
     ST_FALLBACK,
+    ST_SEED_PAIRS,
     ST_NSTAT
 };
 

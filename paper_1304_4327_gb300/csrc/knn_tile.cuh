@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
     // counters: one atomic per thread that holds any
     if (n_skip) atomicAdd(&a.stats[ST_SKIPPED], n_skip);
     if (n_eval) atomicAdd(&a.stats[ST_EVALUATED], n_eval);
-    if (n_pp) atomicAdd(&a.stats[ST_POINT_PAIRS], n_pp);
+    if (n_pp) atomicAdd(&a.stats[MODE == MODE_SEED ? ST_SEED_PAIRS : ST_POINT_PAIRS], n_pp);
     if (n_re) atomicAdd(&a.stats[ST_RERANK], n_re);
 }
 

@@ -30,11 +30,12 @@ class dtree_opts(ctypes.Structure):
 STAT_FIELDS = ("node_pairs_scored", "node_pairs_pruned", "leaf_pairs_emitted",
                "leaf_pairs_skipped", "leaf_pairs_evaluated", "point_pairs",
                "rerank_candidates", "fallback_queries", "query_blocks", "kernel_launches",
-               "ns_seed", "ns_traverse", "ns_basecase", "ns_fallback", "fallback64_queries")
+               "ns_seed", "ns_traverse", "ns_basecase", "ns_fallback", "fallback64_queries",
+               "seed_point_pairs")
 
 
 class dtree_stats(ctypes.Structure):
-    _fields_ = [(f, _I64) for f in STAT_FIELDS] + [("reserved", _I64 * 1)]
+    _fields_ = [(f, _I64) for f in STAT_FIELDS]
 
 
 class DTreeError(RuntimeError):
