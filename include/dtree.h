@@ -154,6 +154,39 @@ int dtree_build(const float* pts, int64_t n, int32_t d, const dtree_opts* opts, 
 int dtree_knn(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_idx,
               float* out_dist, const dtree_opts* opts, void* stream, dtree_stats* stats);
 
+/* One problem of a batch: the arguments of one dtree_knn call. */
+typedef struct dtree_problem {
+    const dtree_t* query;   /* NULL (or == ref): monochromatic */
+    const dtree_t* ref;
+    int32_t k;
+    int32_t query_block;    /* queries per block of this problem, 16..128, or 0 for
+                               opts->query_block */
+    int64_t* out_idx;       /* device, n_q x k */
+    float* out_dist;        /* device, n_q x k */
+} dtree_problem;
+
+/*
+ * dtree_knn_batch -- many independent kNN problems (Section 5's problem, as in
+ * dtree_knn) in one call.  Problems whose points share a width bucket
+ * (d <= 4, 8, 16, 32, 64) run together: each phase of the search (seed,
+ * bounds, traversal levels, BaseCase tiles, re-rank, fallback) is one launch
+ * over all their blocks, pairs and queries, so a batch of small problems
+ * fills the GPU as one large problem would.  The lists of a group are sized
+ * for its largest k.
+ *   nprob     number of problems (0 returns DTREE_OK)
+ *   probs     host array of nprob problems; their trees must live on the
+ *             current device and each problem's outputs must not overlap
+ *             another's
+ *   opts      as in dtree_knn, shared by every problem
+ *   stats     nullable; counters summed over the batch
+ * Results are exactly those of one dtree_knn call per problem.  Status: the
+ * first failing problem's argument check (nothing is launched), or the
+ * search's status.  Waits for the result.  (The paper runs one problem at
+ * a time; batching is this library's addition.)
+ */
+int dtree_knn_batch(int32_t nprob, const dtree_problem* probs, const dtree_opts* opts,
+                    void* stream, dtree_stats* stats);
+
 /*
  * dtree_knn_noalloc -- dtree_knn with no device allocation: the same search,
  * arguments, results and status codes, but every scratch buffer the call

@@ -83,79 +83,128 @@ __device__ __forceinline__ float box_dmin_down(const float* a, const float* b) {
 }
 
 template <int DP>
-__global__ void k_seed(const float* qbox, const float* rbox, int64_t qblock0, int nblocks, int Ls,
-                       int hr, int32_t* seed_leaf0, int32_t* seed_nleaf) {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nblocks) return;
-    const float* qb = qbox + (qblock0 + b) * 2 * DP;
+__global__ void k_seed(const ProbDev* probs, const int32_t* blk_prob, int nblocks,
+                       int32_t* seed_leaf0, int32_t* seed_nleaf) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nblocks) return;
+    const ProbDev& P = probs[blk_prob[g]];
+    const float* qb = P.qbox + (P.qblock0 + (g - P.block0)) * 2 * DP;
+    const float* rbox = P.rbox;
     float c[DP];
 #pragma unroll
     for (int j = 0; j < DP; ++j) c[j] = 0.5f * (qb[j] + qb[DP + j]);
     int64_t n = 0;
-    for (int L = 0; L < Ls; ++L) {
+    for (int L = 0; L < P.Ls; ++L) {
         int64_t l = 2 * n + 1, r = l + 1;
         float dl = point_box_d2<DP>(c, rbox + l * 2 * DP);
         float dr = point_box_d2<DP>(c, rbox + r * 2 * DP);
         n = dr < dl ? r : l;
     }
-    int span = hr - Ls;
-    seed_leaf0[b] = (int32_t)(((n + 1) << span) - 1 - (((int64_t)1 << hr) - 1));
-    seed_nleaf[b] = 1 << span;
+    const int span = P.hr - P.Ls;
+    seed_leaf0[g] = (int32_t)(((n + 1) << span) - 1 - P.rleaf0);
+    seed_nleaf[g] = 1 << span;
 }
 
+constexpr int kExpandProbs = 64;
+
 template <int DP>
-__global__ void __launch_bounds__(256) k_expand(const float* __restrict__ qbox,
-                                                const float* __restrict__ rbox,
-                                                const float* __restrict__ Bq, const int2* fin,
+__global__ void __launch_bounds__(256) k_expand(const ProbDev* __restrict__ probs,
+                                                const int32_t* __restrict__ node_prob,
+                                                const float* __restrict__ Bn, const int2* fin,
                                                 const int* nin, int2* fout, int* nout, int64_t cap,
                                                 int4* outp, int* noutp, int64_t capp, int* bcount,
-                                                int Lb, int hr, int64_t qblock0, int64_t rleaf0,
                                                 const int32_t* sl0, const int32_t* sn, int* overflow,
-                                                unsigned long long* stats) {
+                                                unsigned long long* stats, int np) {
+    // the first kExpandProbs problems' descriptors are staged in shared memory
+    extern __shared__ ProbDev sprob[];
+    for (int p = threadIdx.x; p < min(np, kExpandProbs); p += blockDim.x) sprob[p] = probs[p];
+    __syncthreads();
     const int n = (int)min((int64_t)*nin, cap);  // the counter runs past cap on overflow
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     unsigned long long sc = 0, pr = 0, em = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int2 p = fin[i];
-        int lq = level_of_node(p.x), lr = level_of_node(p.y);
-        bool cq = lq < Lb, cr = lr < hr;
-        bool qbot = (cq ? lq + 1 : lq) == Lb, rbot = (cr ? lr + 1 : lr) == hr;
-        for (int a = 0; a < (cq ? 2 : 1); ++a) {
-            int64_t qc = cq ? 2 * (int64_t)p.x + 1 + a : p.x;
-            float B = Bq[qc];
-            const float* qbx = qbox + qc * 2 * DP;
-            for (int b = 0; b < (cr ? 2 : 1); ++b) {
-                int64_t rc = cr ? 2 * (int64_t)p.y + 1 + b : p.y;
-                float dmin = box_dmin_down<DP>(qbx, rbox + rc * 2 * DP);
+    // Warps walk the frontier in step.  Each frontier pair has up to four
+    // child pairs (slot s = 2a + b); slot by slot, every lane scores its child
+    // and the warp appends the slot's candidates and frontier pairs with one
+    // atomic each, in lane order: every lane's first child, then every lane's
+    // second child, ...  (the order of per-thread appends, which keeps the
+    // traversal's spatial order in the lists).
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int i = base + lane;
+        const bool live = i < n;
+        int2 pq = make_int2(0, 0);
+        const ProbDev* Pp = sprob;
+        if (live) {
+            pq = fin[i];  // (global query node, reference node)
+            const int pi = np == 1 ? 0 : node_prob[pq.x];
+            Pp = pi < kExpandProbs ? &sprob[pi] : &probs[pi];
+        }
+        // the problem's fields, read once
+        const int64_t node0 = Pp->node0, qblock0 = Pp->qblock0, rleaf0 = Pp->rleaf0;
+        const float* __restrict__ qbox = Pp->qbox;
+        const float* __restrict__ rbox = Pp->rbox;
+        const int Lb = Pp->Lb, hr = Pp->hr, block0 = Pp->block0;
+        const int64_t qloc = pq.x - node0;
+        const int lq = level_of_node(qloc), lr = level_of_node(pq.y);
+        const bool cq = lq < Lb, cr = lr < hr;
+        const bool qbot = (cq ? lq + 1 : lq) == Lb, rbot = (cr ? lr + 1 : lr) == hr;
+#pragma unroll 1
+        for (int slot = 0; slot < 4; ++slot) {
+            const int a = slot >> 1, b = slot & 1;
+            bool do_emit = false, do_push = false;
+            int4 e4 = make_int4(0, 0, 0, 0);
+            int2 f2 = make_int2(0, 0);
+            if (live && (a == 0 || cq) && (b == 0 || cr)) {
+                const int64_t qc = cq ? 2 * qloc + 1 + a : qloc;
+                const int64_t rc = cr ? 2 * (int64_t)pq.y + 1 + b : pq.y;
+                const float* qbx = qbox + qc * 2 * DP;
+                const float* rbx = rbox + rc * 2 * DP;
+                const float dmin = box_dmin_down<DP>(qbx, rbx);
                 ++sc;
-                if (dmin > B) {  // Score() = infinity: prune every descendant pair
+                if (dmin > Bn[node0 + qc]) {  // Score() = infinity: prune every descendant pair
                     ++pr;
-                    continue;
-                }
-                if (qbot && rbot) {
-                    int blk = (int)(qc - qblock0), leaf = (int)(rc - rleaf0);
-                    int s0 = sl0[blk];
-                    if (leaf >= s0 && leaf < s0 + sn[blk]) continue;  // evaluated by the seed
-                    int pos = atomicAdd(noutp, 1);
-                    if (pos < capp) {
+                } else if (qbot && rbot) {
+                    const int blk = block0 + (int)(qc - qblock0);
+                    const int leaf = (int)(rc - rleaf0);
+                    const int s0 = sl0[blk];
+                    if (!(leaf >= s0 && leaf < s0 + sn[blk])) {  // else evaluated by the seed
                         // evaluation order: squared distance between the box centres
-                        const float* rbx = rbox + rc * 2 * DP;
                         float o = 0.f;
 #pragma unroll
                         for (int j = 0; j < DP; ++j) {
                             float t = 0.5f * (qbx[j] + qbx[DP + j]) - 0.5f * (rbx[j] + rbx[DP + j]);
                             o = fmaf(t, t, o);
                         }
-                        outp[pos] = make_int4(blk, leaf, __float_as_int(dmin), __float_as_int(o));
-                        atomicAdd(&bcount[blk], 1);
-                        ++em;
-                    } else {
-                        *overflow = 1;
+                        e4 = make_int4(blk, leaf, __float_as_int(dmin), __float_as_int(o));
+                        do_emit = true;
                     }
                 } else {
-                    int pos = atomicAdd(nout, 1);
-                    if (pos < cap) fout[pos] = make_int2((int)qc, (int)rc);
-                    else *overflow = 1;
+                    f2 = make_int2((int)(node0 + qc), (int)rc);
+                    do_push = true;
                 }
+            }
+            const unsigned me = __ballot_sync(0xffffffffu, do_emit);
+            const unsigned mf = __ballot_sync(0xffffffffu, do_push);
+            int be = 0, bf = 0;
+            if (lane == 0) {
+                if (me) be = atomicAdd(noutp, __popc(me));
+                if (mf) bf = atomicAdd(nout, __popc(mf));
+            }
+            be = __shfl_sync(0xffffffffu, be, 0) + __popc(me & lt);
+            bf = __shfl_sync(0xffffffffu, bf, 0) + __popc(mf & lt);
+            if (do_emit) {
+                if (be < capp) {
+                    outp[be] = e4;
+                    atomicAdd(&bcount[e4.x], 1);
+                    ++em;
+                } else {
+                    *overflow = 1;
+                }
+            }
+            if (do_push) {
+                if (bf < cap) fout[bf] = f2;
+                else *overflow = 1;
             }
         }
     }
@@ -177,19 +226,20 @@ __global__ void k_fill(float* p, int64_t n, float v) {
     if (i < n) p[i] = v;
 }
 
-// One warp per block: B_1 / A of the block from its queries' k-th keys, then
-// pushed to every ancestor with monotone atomics (non-negative floats order
-// like their bit patterns).
-__global__ void k_block_bounds(const float* qub, const int32_t* qbeg, const int32_t* qcnt,
-                               int64_t qblock0, int nblocks, float* B1n, float* An) {
-    int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-    int lane = threadIdx.x & 31;
+// One warp per block: B_1 / A of the block from its queries' upper bounds on
+// their k-th distances, then pushed to every ancestor with monotone atomics
+// (non-negative floats order like their bit patterns).
+__global__ void k_block_bounds(const ProbDev* probs, const int32_t* blk_prob, int nblocks,
+                               const float* qub, float* B1n, float* An) {
+    const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (w >= nblocks) return;
-    int64_t node = qblock0 + w;
-    int b = qbeg[node], c = qcnt[node];
+    const ProbDev& P = probs[blk_prob[w]];
+    const int64_t node = P.qblock0 + (w - P.block0);
+    const int b = P.qbeg[node], c = P.qcnt[node];
     float mx = 0.f, mn = INFINITY;
     for (int i = lane; i < c; i += 32) {
-        float ub = qub[b + i];
+        const float ub = qub[P.q0 + b + i];
         mx = fmaxf(mx, ub);
         mn = fminf(mn, ub);
     }
@@ -199,23 +249,25 @@ __global__ void k_block_bounds(const float* qub, const int32_t* qbeg, const int3
         mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
     }
     if (lane == 0) {
-        B1n[node] = mx;
-        An[node] = mn;
+        B1n[P.node0 + node] = mx;
+        An[P.node0 + node] = mn;
         for (int64_t p = node; p > 0;) {
             p = (p - 1) / 2;
-            atomicMax(reinterpret_cast<int*>(&B1n[p]), __float_as_int(mx));
-            atomicMin(reinterpret_cast<int*>(&An[p]), __float_as_int(mn));
+            atomicMax(reinterpret_cast<int*>(&B1n[P.node0 + p]), __float_as_int(mx));
+            atomicMin(reinterpret_cast<int*>(&An[P.node0 + p]), __float_as_int(mn));
         }
     }
 }
 
-__global__ void k_node_bounds(const float* B1n, const float* An, const float* lam, int64_t nn,
-                              float* Bn) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// B(N) = min over N and its ancestors a of min(B_1(a), A(a) + 2 lambda(a)).
+__global__ void k_node_bounds(const ProbDev* probs, const int32_t* node_prob, const float* B1n,
+                              const float* An, int64_t nn, float* Bn) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nn) return;
+    const ProbDev& P = probs[node_prob[i]];
     float B = INFINITY;
-    for (int64_t a = i;; a = (a - 1) / 2) {
-        B = fminf(B, fminf(B1n[a], __fadd_ru(An[a], 2.f * lam[a])));
+    for (int64_t a = i - P.node0;; a = (a - 1) / 2) {
+        B = fminf(B, fminf(B1n[P.node0 + a], __fadd_ru(An[P.node0 + a], 2.f * P.qlam[a])));
         if (a == 0) break;
     }
     Bn[i] = B;
@@ -245,6 +297,7 @@ __global__ void __launch_bounds__(1024) k_scan(const int* cnt, int n, int64_t* o
     if (threadIdx.x == 0) off[n] = carry;
 }
 
+// Scatter the candidate pairs into the per-block CSR.
 __global__ void k_csr_fill(const int4* outp, int np, const int64_t* off, int* cur, int32_t* leaf,
                            float* dmin, float* key) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -256,24 +309,81 @@ __global__ void k_csr_fill(const int4* outp, int np, const int64_t* off, int* cu
     key[pos] = __int_as_float(e.w);
 }
 
+// Order each block's candidate leaves for the BaseCase pass: the list keeps
+// the traversal's order (leaves of one subtree together) in windows of
+// kCsrSortCap, and each window is sorted by its order key (the squared
+// distance between the block's and the leaf's box centres).  One CTA per
+// block at a time, a bitonic sort per window in shared memory.
+constexpr int kCsrSortCap = 1024;  // the window index takes the key's low bits
+constexpr size_t kCsrSortSmem = (size_t)kCsrSortCap * (8 + 4 + 4);
+
+__global__ void __launch_bounds__(256) k_csr_sort(const int64_t* off, int nb, int32_t* leaf,
+                                                  float* dmin, const float* key) {
+    extern __shared__ __align__(16) unsigned char csm[];
+    uint64_t* sk = reinterpret_cast<uint64_t*>(csm);
+    int32_t* tl = reinterpret_cast<int32_t*>(sk + kCsrSortCap);
+    float* td = reinterpret_cast<float*>(tl + kCsrSortCap);
+    const int tid = threadIdx.x;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int64_t o0 = off[b], n = off[b + 1] - o0;  // uniform in the CTA
+        for (int64_t w0 = 0; w0 + 1 < n; w0 += kCsrSortCap) {
+            const int wn = (int)(n - w0 < kCsrSortCap ? n - w0 : kCsrSortCap);
+            int np2 = 1;
+            while (np2 < wn) np2 <<= 1;
+            for (int i = tid; i < np2; i += blockDim.x) {
+                uint64_t v = ~0ull;
+                if (i < wn) {
+                    const int64_t c = o0 + w0 + i;
+                    v = ((uint64_t)f2o(key[c]) << 32) | (uint32_t)i;
+                    tl[i] = leaf[c];
+                    td[i] = dmin[c];
+                }
+                sk[i] = v;
+            }
+            __syncthreads();
+            for (int kk = 2; kk <= np2; kk <<= 1)
+                for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                    for (int t = tid; t < np2 / 2; t += blockDim.x) {
+                        const int i = 2 * t - (t & (jj - 1));
+                        const int l = i + jj;
+                        const bool up = (i & kk) == 0;
+                        const uint64_t x = sk[i], y = sk[l];
+                        if ((x > y) == up) {
+                            sk[i] = y;
+                            sk[l] = x;
+                        }
+                    }
+                    __syncthreads();
+                }
+            for (int i = tid; i < wn; i += blockDim.x) {
+                const int j = (int)(uint32_t)sk[i];  // the window index (i < kCsrSortCap)
+                const int64_t c = o0 + w0 + i;
+                leaf[c] = tl[j];
+                dmin[c] = td[j];
+            }
+            __syncthreads();
+        }
+    }
+}
+
 }  // namespace
 
 template <int DP>
-int launch_expand(const float* qbox, const float* rbox, const float* Bq, const int2* fin,
+int launch_expand(const ProbDev* probs, const int32_t* node_prob, const float* Bn, const int2* fin,
                   const int* nin, int2* fout, int* nout, int64_t cap, int4* outp, int* noutp,
-                  int64_t capp, int* bcount, int Lb, int hr, int64_t qblock0, int64_t rleaf0,
-                  const int32_t* sl0, const int32_t* sn, int* overflow, unsigned long long* stats,
-                  int grid, cudaStream_t s) {
-    DT_LAUNCH(k_expand<DP>, grid, 256, 0, s, qbox, rbox, Bq, fin, nin, fout, nout, cap, outp, noutp,
-              capp, bcount, Lb, hr, qblock0, rleaf0, sl0, sn, overflow, stats);
+                  int64_t capp, int* bcount, const int32_t* sl0, const int32_t* sn, int* overflow,
+                  unsigned long long* stats, int np, int grid, cudaStream_t s) {
+    const size_t smem = (size_t)std::min(np, kExpandProbs) * sizeof(ProbDev);
+    DT_LAUNCH(k_expand<DP>, grid, 256, smem, s, probs, node_prob, Bn, fin, nin, fout, nout, cap,
+              outp, noutp, capp, bcount, sl0, sn, overflow, stats, np);
     return DTREE_OK;
 }
 
 template <int DP>
-int launch_seed(const float* qbox, const float* rbox, int64_t qblock0, int nblocks, int Ls, int hr,
+int launch_seed(const ProbDev* probs, const int32_t* blk_prob, int nblocks,
                 int32_t* seed_leaf0, int32_t* seed_nleaf, cudaStream_t s) {
-    DT_LAUNCH(k_seed<DP>, (nblocks + 127) / 128, 128, 0, s, qbox, rbox, qblock0, nblocks, Ls, hr,
-              seed_leaf0, seed_nleaf);
+    DT_LAUNCH(k_seed<DP>, (nblocks + 127) / 128, 128, 0, s, probs, blk_prob, nblocks, seed_leaf0,
+              seed_nleaf);
     return DTREE_OK;
 }
 
@@ -366,173 +476,250 @@ struct Pool {
         if (rc_ != DTREE_OK) return rc_; \
     } while (0)
 
+
+// Per block, query node and work item of a batch: the problem it belongs to
+// (problems are laid out in order, so each lookup is a binary search over
+// the problems' first entries), plus the traversal's root pairs.
+__global__ void k_index(const ProbDev* probs, int np, int nb, int64_t nn, int ni,
+                        int32_t* blk_prob, int32_t* node_prob, int2* items, int2* roots) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    auto find = [&](int64_t x, int which) {
+        int lo = 0, hi = np - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            const int64_t first = which == 0 ? probs[mid].block0 : which == 1 ? probs[mid].node0
+                                                                              : probs[mid].item0;
+            if (first <= x) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    };
+    if (t < nb) blk_prob[t] = find(t, 0);
+    if (t < nn) node_prob[t] = find(t, 1);
+    if (t < ni) {
+        const int p = find(t, 2);
+        const int local = (int)(t - probs[p].item0);
+        items[t] = make_int2(probs[p].block0 + local / probs[p].cpb, local % probs[p].cpb);
+    }
+    if (t < np) roots[t] = make_int2((int)probs[t].node0, 0);
+}
+
+// One problem of a batch on the host side.
+struct HostProb {
+    const dtree_t* tq;
+    const dtree_t* tr;
+    bool mono;
+    int k;
+    int64_t* out_idx;
+    float* out_dist;
+    int qb;  // queries per block, or 0 for the call's option
+};
+
 // Candidate-list lengths come in buckets of 4, 8, 16, 24 and 32.
 inline int kc_bucket(int need) {
     return need <= 4 ? 4 : need <= 8 ? 8 : need <= 16 ? 16 : need <= 24 ? 24 : 32;
 }
 
+// The search for a batch of problems whose points share the padded dimension
+// DP: every phase is one launch (or one per traversal level) over all the
+// problems' blocks, pairs and queries.
 template <int DP>
-int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* out_idx,
-             float* out_dist, int qb_cap, int seed_pts, int prec, int spin, cudaStream_t s,
-             dtree_stats* st, const ScratchArena* arena) {
+int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int prec, int spin,
+                   cudaStream_t s, dtree_stats* st, const ScratchArena* arena) {
     const int64_t launches0 = g_launches.load();
-    const int64_t nq = tq->n, m = tr->n;
-    const int Lb = std::min<int>(tq->height, level_of_count(nq, qb_cap));
-    const int nblocks = 1 << Lb;
-    const int64_t qblock0 = nblocks - 1;
-    const int64_t maxcnt = (nq + nblocks - 1) / nblocks;
-    const int cpb = (int)((maxcnt + kQB - 1) / kQB);
-    const int hr = tr->height;
-    const int64_t rleaf0 = ((int64_t)1 << hr) - 1;
-    // list length: room for k plus the candidates inside the error band (the
-    // tensor-core band is wider, so its lists are longer)
     const int fmt = prec == DTREE_PREC_BF16 ? 1 : prec == DTREE_PREC_TF32 ? 2 : 0;
     // list length: k plus room for the candidates inside the error band
     // (TF32 and split BF16 bands ~1% of d^2 at d=16, single BF16 ~5%, used
     // beyond 32 dimensions); buckets 4, 8, 16, 24, 32
-    const int kc_need = fmt == 1 ? (DP <= 32 ? k + 14 : 2 * k + 12) : fmt == 2 ? k + 14 : k + 1;
+    int kmax = 0;
+    for (int i = 0; i < np; ++i) kmax = std::max(kmax, hp[i].k);
+    if (kmax + 1 > 32) return DTREE_ERR_UNSUPPORTED;
+    const int kc_need = fmt == 1 ? (DP <= 32 ? kmax + 14 : 2 * kmax + 12) : fmt == 2 ? kmax + 14 : kmax + 1;
     const int KC = kc_bucket(kc_need);
-    if (k + 1 > 32) return DTREE_ERR_UNSUPPORTED;
-    int Ls = 0;
-    while (Ls < hr && (m >> (Ls + 1)) >= seed_pts) ++Ls;
+
+    // the problems' layout in the batch-wide arrays
+    ProbDev one[1];
+    std::vector<ProbDev> many;
+    ProbDev* pd = one;
+    if (np > 1) {
+        many.resize(np);
+        pd = many.data();
+    }
+    int64_t NQ = 0, NN = 0;
+    int NB = 0, NI = 0, steps = 1;
+    for (int i = 0; i < np; ++i) {
+        const dtree_t *tq = hp[i].tq, *tr = hp[i].tr;
+        ProbDev& P = pd[i];
+        memset(&P, 0, sizeof(P));
+        const int64_t nq = tq->n, m = tr->n;
+        P.Lb = std::min<int>(tq->height, level_of_count(nq, hp[i].qb > 0 ? hp[i].qb : qb_cap));
+        P.nblocks = 1 << P.Lb;
+        P.qblock0 = P.nblocks - 1;
+        const int64_t maxcnt = (nq + P.nblocks - 1) / P.nblocks;
+        P.cpb = (int)((maxcnt + kQB - 1) / kQB);
+        P.hr = tr->height;
+        P.rleaf0 = ((int64_t)1 << P.hr) - 1;
+        P.Ls = 0;
+        const int seed = std::max(hp[i].k + 1, seed_pts);
+        while (P.Ls < P.hr && (m >> (P.Ls + 1)) >= seed) ++P.Ls;
+        P.qpts = tq->pts;
+        P.qidx = tq->idx;
+        P.qbeg = tq->nbeg;
+        P.qcnt = tq->ncnt;
+        P.qlam = tq->lam;
+        P.qbox = tq->box;
+        P.rpts = tr->pts;
+        P.ridx = tr->idx;
+        P.rbeg = tr->nbeg;
+        P.rcnt = tr->ncnt;
+        P.rbox = tr->box;
+        P.out_idx = hp[i].out_idx;
+        P.out_dist = hp[i].out_dist;
+        P.k = hp[i].k;
+        P.mono = hp[i].mono ? 1 : 0;
+        P.q0 = NQ;
+        P.node0 = NN;
+        P.block0 = NB;
+        P.item0 = NI;
+        NQ += nq;
+        NN += 2 * (int64_t)P.nblocks - 1;
+        NB += P.nblocks;
+        NI += P.nblocks * P.cpb;
+        steps = std::max(steps, std::max(P.Lb, P.hr));
+    }
+    if (NB > (1 << 30) || NI > (1 << 30) || NN > (1 << 30)) return DTREE_ERR_UNSUPPORTED;
 
     Pool P;
     P.s = s;
     P.arena = arena;
-    int32_t *sl0, *sn, *cand_i, *csr_leaf = nullptr;
+    ProbDev* probs;
+    int32_t *blk_prob, *node_prob, *sl0, *sn, *cand_i, *csr_leaf = nullptr;
+    int2 *items, *roots;
     int4 *fbq_list, *fbq2_list;
-    float *cand_d, *B1n, *An, *Bn, *csr_dmin = nullptr, *csr_key = nullptr;
-    int *ctr, *bcount, *bcur;
+    float *cand_d, *B1n, *An, *Bn, *csr_dmin = nullptr, *csr_key = nullptr, *qub;
+    int *ctr, *bcount, *bcur, *derr;
     int64_t* off;
     unsigned long long* dstats;
-    const int64_t nqn = 2 * (int64_t)nblocks - 1;
-    DT_TRY(P.get(&sl0, nblocks));
-    DT_TRY(P.get(&sn, nblocks));
-    DT_TRY(P.get(&cand_d, (size_t)KC * nq));
-    DT_TRY(P.get(&cand_i, (size_t)KC * nq));
-    float* qub;
-    int* derr;
-    DT_TRY(P.get(&qub, nq));
+    DT_TRY(P.get(&probs, np));
+    DT_TRY(P.get(&blk_prob, NB));
+    DT_TRY(P.get(&node_prob, NN));
+    DT_TRY(P.get(&items, NI));
+    DT_TRY(P.get(&roots, np));
+    DT_TRY(P.get(&sl0, NB));
+    DT_TRY(P.get(&sn, NB));
+    DT_TRY(P.get(&cand_d, (size_t)KC * NQ));
+    DT_TRY(P.get(&cand_i, (size_t)KC * NQ));
+    DT_TRY(P.get(&qub, NQ));
     DT_TRY(P.get(&derr, 1));
-    DT_CHECK(cudaMemsetAsync(derr, 0, sizeof(int), s));
-    DT_TRY(P.get(&B1n, nqn));
-    DT_TRY(P.get(&An, nqn));
-    DT_TRY(P.get(&Bn, nqn));
-    // 0-2 work counters, 3 fb count, 4 overflow, 5-6 frontier, 7 pairs, 8 fb2 count, 9 work
+    DT_TRY(P.get(&B1n, NN));
+    DT_TRY(P.get(&An, NN));
+    DT_TRY(P.get(&Bn, NN));
+    // 0-2 work counters, 3 fallback count, 4 overflow, 5-6 frontier, 7 pairs, 8 fallback-64 count
     DT_TRY(P.get(&ctr, 16));
-    DT_TRY(P.get(&bcount, nblocks));
-    DT_TRY(P.get(&bcur, nblocks));
-    DT_TRY(P.get(&fbq_list, nq));
-    DT_TRY(P.get(&fbq2_list, nq));
-    DT_TRY(P.get(&off, nblocks + 1));
+    DT_TRY(P.get(&bcount, NB));
+    DT_TRY(P.get(&bcur, NB));
+    DT_TRY(P.get(&fbq_list, NQ));
+    DT_TRY(P.get(&fbq2_list, NQ));
+    DT_TRY(P.get(&off, NB + 1));
     DT_TRY(P.get(&dstats, ST_NSTAT));
+    DT_CHECK(cudaMemsetAsync(derr, 0, sizeof(int), s));
     DT_CHECK(cudaMemsetAsync(ctr, 0, 16 * sizeof(int), s));
-
     DT_CHECK(cudaMemsetAsync(dstats, 0, ST_NSTAT * sizeof(unsigned long long), s));
+    DT_CHECK(cudaMemcpyAsync(probs, pd, np * sizeof(ProbDev), cudaMemcpyHostToDevice, s));
+    {
+        const int64_t nmax = std::max<int64_t>(std::max<int64_t>(NB, NN), std::max<int64_t>(NI, np));
+        DT_LAUNCH(k_index, (int)((nmax + 255) / 256), 256, 0, s, probs, np, NB, NN, NI, blk_prob,
+                  node_prob, items, roots);
+    }
     PhaseTimer tm(s, st != nullptr);
     tm.mark();  // 0
 
     // 1. seed
-    DT_TRY(launch_seed<DP>(tq->box, tr->box, qblock0, nblocks, Ls, hr, sl0, sn, s));
+    DT_TRY(launch_seed<DP>(probs, blk_prob, NB, sl0, sn, s));
     TileArgs a{};
-    a.qpts = tq->pts;
-    a.qidx = tq->idx;
-    a.qbeg = tq->nbeg;
-    a.qcnt = tq->ncnt;
-    a.qlam = tq->lam;
-    a.qbox = tq->box;
-    a.qblock0 = qblock0;
-    a.nq = nq;
-    a.cpb = cpb;
-    a.rpts = tr->pts;
-    a.ridx = tr->idx;
-    a.rbeg = tr->nbeg;
-    a.rcnt = tr->ncnt;
-    a.rbox = tr->box;
-    a.rleaf0 = rleaf0;
-    a.k = k;
-    a.mono = mono ? 1 : 0;
+    a.probs = probs;
+    a.blk_prob = blk_prob;
+    a.items = items;
+    a.nitems = NI;
+    a.nq_all = NQ;
     a.seed_leaf0 = sl0;
     a.seed_nleaf = sn;
     a.cand_d = cand_d;
     a.cand_i = cand_i;
     a.qub = qub;
-    a.nwork = nblocks;
-    a.out_idx = out_idx;
-    a.out_dist = out_dist;
     a.fbq_list = fbq_list;
     a.fbq_count = ctr + 3;
     a.fbq2_list = fbq2_list;
     a.fbq2_count = ctr + 8;
     a.stats = dstats;
     a.work_ctr = ctr + 0;
-    auto tile = [&](int mode, int items) -> int {
-        if (fmt)
-            return launch_tile_tc<DP>(a, fmt, KC, mode, items, derr, spin, s);
-        return launch_tile_cc<DP>(a, KC, mode, items, s);
-    };
     // the seed pass runs on the CUDA cores whatever the precision: its lists
     // start empty, so nearly every early candidate is an insertion, which the
     // float32 tile does cheaply; its keys (relative error <= rel_eps) are
-    // tighter than any tensor-core key, so the main pass's bounds hold for them
-    // with lists of bucket(k + 1) entries (the float32 band needs no more)
+    // tighter than any tensor-core key, so the main pass's bounds hold for
+    // them.  It keeps lists of bucket(k + 1) entries (the float32 band needs
+    // no more); the main pass's other rows start empty.
     a.kc_rows = KC;
-    DT_TRY(launch_tile_cc<DP>(a, kc_bucket(k + 1), MODE_SEED, nblocks * cpb, s));
+    DT_TRY(launch_tile_cc<DP>(a, kc_bucket(kmax + 1), MODE_SEED, NI, s));
     tm.mark();  // 1
 
     // 2. bounds of every query node down to the blocks
-    DT_LAUNCH(k_fill, (int)((nqn + 255) / 256), 256, 0, s, B1n, nqn, 0.f);
-    DT_LAUNCH(k_fill, (int)((nqn + 255) / 256), 256, 0, s, An, nqn, INFINITY);
-    DT_LAUNCH(k_block_bounds, (nblocks * 32 + 255) / 256, 256, 0, s, qub, tq->nbeg, tq->ncnt,
-              qblock0, nblocks, B1n, An);
-    DT_LAUNCH(k_node_bounds, (int)((nqn + 255) / 256), 256, 0, s, B1n, An, tq->lam, nqn, Bn);
+    DT_LAUNCH(k_fill, (int)((NN + 255) / 256), 256, 0, s, B1n, NN, 0.f);
+    DT_LAUNCH(k_fill, (int)((NN + 255) / 256), 256, 0, s, An, NN, INFINITY);
+    DT_LAUNCH(k_block_bounds, (NB * 32 + 255) / 256, 256, 0, s, probs, blk_prob, NB, qub, B1n, An);
+    DT_LAUNCH(k_node_bounds, (int)((NN + 255) / 256), 256, 0, s, probs, node_prob, B1n, An, NN, Bn);
 
     // 3. level-synchronous pruning dual-tree traversal
-    const int steps = std::max(1, std::max(Lb, hr));
-    int64_t cap = std::max<int64_t>(tr->cap_hint, std::max<int64_t>(1 << 20, (int64_t)nblocks * 256));
+    int64_t cap = std::max<int64_t>(1 << 20, (int64_t)NB * 256);
+    if (np == 1) cap = std::max<int64_t>(cap, hp[0].tr->cap_hint);
     if (arena) {
         // a fixed range: the pair buffers take what is left, once (the three
         // blocks' alignment costs at most 3 x 255 bytes)
         const size_t per = sizeof(int4) + 2 * sizeof(int2);
         const size_t room = P.left();
         cap = room > 1024 ? (int64_t)std::min<size_t>((room - 1024) / per, (size_t)1 << 30) : 0;
-        if (cap < 1) return DTREE_ERR_TOO_LARGE;
+        if (cap < np) return DTREE_ERR_TOO_LARGE;
     }
-    const int egrid = occupancy_grid((const void*)k_expand<DP>, 256, 0);
-    int np = 0;
+    const int egrid = occupancy_grid((const void*)k_expand<DP>, 256,
+                                     (size_t)std::min(np, kExpandProbs) * sizeof(ProbDev));
+    int npairs = 0;
     int4* outp = nullptr;
-    auto finish_csr = [&](int npairs) -> int {
-        np = npairs;
-        DT_TRY(P.get(&csr_leaf, std::max(np, 1)));
-        DT_TRY(P.get(&csr_dmin, std::max(np, 1)));
-        DT_TRY(P.get(&csr_key, std::max(np, 1)));
-        DT_LAUNCH(k_scan, 1, 1024, 0, s, bcount, nblocks, off);
-        DT_CHECK(cudaMemsetAsync(bcur, 0, nblocks * sizeof(int), s));
-        if (np > 0)
-            DT_LAUNCH(k_csr_fill, (np + 255) / 256, 256, 0, s, outp, np, off, bcur, csr_leaf,
+    auto finish_csr = [&](int n) -> int {
+        npairs = n;
+        DT_TRY(P.get(&csr_leaf, std::max(npairs, 1)));
+        DT_TRY(P.get(&csr_dmin, std::max(npairs, 1)));
+        DT_TRY(P.get(&csr_key, std::max(npairs, 1)));
+        DT_LAUNCH(k_scan, 1, 1024, 0, s, bcount, NB, off);
+        DT_CHECK(cudaMemsetAsync(bcur, 0, NB * sizeof(int), s));
+        if (npairs > 0) {
+            DT_LAUNCH(k_csr_fill, (npairs + 255) / 256, 256, 0, s, outp, npairs, off, bcur, csr_leaf,
                       csr_dmin, csr_key);
+            DT_CHECK(cudaFuncSetAttribute(k_csr_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kCsrSortSmem));
+            const int sgrid = std::min(NB, occupancy_grid((const void*)k_csr_sort, 256, kCsrSortSmem));
+            DT_LAUNCH(k_csr_sort, sgrid, 256, kCsrSortSmem, s, off, NB, csr_leaf, csr_dmin, csr_key);
+        }
+        P.release(csr_key);  // only the order needed it
         P.release(outp);
         return DTREE_OK;
     };
-    const int2 root = make_int2(0, 0);
-    const int one = 1;
     if (!arena) {
         // Buffers sized level by level: a frontier pair has at most four child
         // pairs, so before each level the output frontier and the candidate
         // buffer get room for four times the current frontier (the frontier
         // size is read back after every level).
         int2* F[2];
-        int64_t fcap[2] = {cap, cap}, ocap = cap;
+        int64_t fcap[2] = {std::max<int64_t>(cap, np), std::max<int64_t>(cap, np)}, ocap = cap;
         DT_TRY(P.get(&outp, ocap));
         DT_TRY(P.get(&F[0], fcap[0]));
         DT_TRY(P.get(&F[1], fcap[1]));
-        DT_CHECK(cudaMemsetAsync(bcount, 0, nblocks * sizeof(int), s));
+        DT_CHECK(cudaMemsetAsync(bcount, 0, NB * sizeof(int), s));
         DT_CHECK(cudaMemsetAsync(ctr + 4, 0, 4 * sizeof(int), s));
-        DT_CHECK(cudaMemcpyAsync(F[0], &root, sizeof(int2), cudaMemcpyHostToDevice, s));
-        DT_CHECK(cudaMemcpyAsync(ctr + 5, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+        DT_CHECK(cudaMemcpyAsync(F[0], roots, np * sizeof(int2), cudaMemcpyDeviceToDevice, s));
+        DT_CHECK(cudaMemcpyAsync(ctr + 5, &np, sizeof(int), cudaMemcpyHostToDevice, s));
         int* nc[2] = {ctr + 5, ctr + 6};
         int cur = 0;
-        int64_t nf = 1, used = 0;
+        int64_t nf = np, used = 0;
         for (int t = 0; t < steps && nf > 0; ++t) {
             const int nx = cur ^ 1;
             const int64_t need = 4 * nf;
@@ -554,9 +741,9 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
                 ocap = oc2;
             }
             DT_CHECK(cudaMemsetAsync(nc[nx], 0, sizeof(int), s));
-            DT_TRY(launch_expand<DP>(tq->box, tr->box, Bn, F[cur], nc[cur], F[nx], nc[nx], fcap[nx],
-                                     outp, ctr + 7, ocap, bcount, Lb, hr, qblock0, rleaf0, sl0, sn,
-                                     ctr + 4, dstats, egrid, s));
+            DT_TRY(launch_expand<DP>(probs, node_prob, Bn, F[cur], nc[cur], F[nx], nc[nx], fcap[nx],
+                                     outp, ctr + 7, ocap, bcount, sl0, sn, ctr + 4, dstats, np,
+                                     egrid, s));
             int hv[4];
             DT_CHECK(cudaMemcpyAsync(hv, ctr + 4, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
             DT_CHECK(cudaStreamSynchronize(s));
@@ -567,7 +754,8 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
         }
         P.release(F[1]);
         P.release(F[0]);
-        cap = std::max(fcap[0], std::max(fcap[1], ocap));
+        if (np == 1)
+            const_cast<dtree_t*>(hp[0].tr)->cap_hint = std::max(fcap[0], std::max(fcap[1], ocap));
         DT_TRY(finish_csr((int)used));
     } else {
         // a fixed range: one pass with the capacity it has left
@@ -577,17 +765,16 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
         DT_TRY(P.get(&outp, cap));
         DT_TRY(P.get(&F0, cap));
         DT_TRY(P.get(&F1, cap));
-        DT_CHECK(cudaMemsetAsync(bcount, 0, nblocks * sizeof(int), s));
+        DT_CHECK(cudaMemsetAsync(bcount, 0, NB * sizeof(int), s));
         DT_CHECK(cudaMemsetAsync(ctr + 4, 0, 4 * sizeof(int), s));
-        DT_CHECK(cudaMemcpyAsync(F0, &root, sizeof(int2), cudaMemcpyHostToDevice, s));
-        DT_CHECK(cudaMemcpyAsync(ctr + 5, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+        DT_CHECK(cudaMemcpyAsync(F0, roots, np * sizeof(int2), cudaMemcpyDeviceToDevice, s));
+        DT_CHECK(cudaMemcpyAsync(ctr + 5, &np, sizeof(int), cudaMemcpyHostToDevice, s));
         int2 *fi = F0, *fo = F1;
         int *ni = ctr + 5, *no = ctr + 6;
         for (int t = 0; t < steps; ++t) {
             DT_CHECK(cudaMemsetAsync(no, 0, sizeof(int), s));
-            DT_TRY(launch_expand<DP>(tq->box, tr->box, Bn, fi, ni, fo, no, cap, outp, ctr + 7, cap,
-                                     bcount, Lb, hr, qblock0, rleaf0, sl0, sn, ctr + 4, dstats,
-                                     egrid, s));
+            DT_TRY(launch_expand<DP>(probs, node_prob, Bn, fi, ni, fo, no, cap, outp, ctr + 7, cap,
+                                     bcount, sl0, sn, ctr + 4, dstats, np, egrid, s));
             std::swap(fi, fo);
             std::swap(ni, no);
         }
@@ -599,17 +786,18 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
         if (hv[0]) return DTREE_ERR_TOO_LARGE;  // the fixed range holds no more pairs
         DT_TRY(finish_csr(hv[3]));
     }
-    if (!arena) const_cast<dtree_t*>(tr)->cap_hint = cap;
     tm.mark();  // 2
 
     // 4. BaseCase over the candidates with the tightening bound, re-rank, output
     a.csr_off = off;
     a.csr_leaf = csr_leaf;
     a.csr_dmin = csr_dmin;
-    a.csr_key = csr_key;
-    a.Bq = Bn + qblock0;
+    a.Bn = Bn;
     a.work_ctr = ctr + 1;
-    DT_TRY(tile(MODE_MAIN, nblocks * cpb));
+    if (fmt)
+        DT_TRY(launch_tile_tc<DP>(a, fmt, KC, MODE_MAIN, NI, derr, spin, s));
+    else
+        DT_TRY(launch_tile_cc<DP>(a, KC, MODE_MAIN, NI, s));
     tm.mark();  // 3
     int nfb = 0, herr = 0;
     DT_CHECK(cudaMemcpyAsync(&nfb, ctr + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -632,54 +820,80 @@ int knn_impl(const dtree_t* tq, const dtree_t* tr, bool mono, int k, int64_t* ou
     DT_CHECK(cudaMemcpyAsync(hs, dstats, sizeof(hs), cudaMemcpyDeviceToHost, s));
     DT_CHECK(cudaStreamSynchronize(s));
     if (st) {
-        memset(st, 0, sizeof(*st));
-        st->node_pairs_scored = (int64_t)hs[ST_SCORED];
-        st->node_pairs_pruned = (int64_t)hs[ST_PRUNED];
-        st->leaf_pairs_emitted = (int64_t)hs[ST_EMITTED];
-        st->leaf_pairs_skipped = (int64_t)hs[ST_SKIPPED];
-        st->leaf_pairs_evaluated = (int64_t)hs[ST_EVALUATED];
-        st->point_pairs = (int64_t)hs[ST_POINT_PAIRS];
-        st->seed_point_pairs = (int64_t)hs[ST_SEED_PAIRS];
-        st->rerank_candidates = (int64_t)hs[ST_RERANK];
-        st->fallback_queries = nfb;
-        st->fallback64_queries = nfb2;
-        st->query_blocks = nblocks;
-        st->kernel_launches = g_launches.load() - launches0;
-        st->ns_seed = tm.ns(0, 1);
-        st->ns_traverse = tm.ns(1, 2);
-        st->ns_basecase = tm.ns(2, 3);
-        st->ns_fallback = tm.ns(3, 4);
+        st->node_pairs_scored += (int64_t)hs[ST_SCORED];
+        st->node_pairs_pruned += (int64_t)hs[ST_PRUNED];
+        st->leaf_pairs_emitted += (int64_t)hs[ST_EMITTED];
+        st->leaf_pairs_skipped += (int64_t)hs[ST_SKIPPED];
+        st->leaf_pairs_evaluated += (int64_t)hs[ST_EVALUATED];
+        st->point_pairs += (int64_t)hs[ST_POINT_PAIRS];
+        st->seed_point_pairs += (int64_t)hs[ST_SEED_PAIRS];
+        st->rerank_candidates += (int64_t)hs[ST_RERANK];
+        st->fallback_queries += nfb;
+        st->fallback64_queries += nfb2;
+        st->query_blocks += NB;
+        st->kernel_launches += g_launches.load() - launches0;
+        st->ns_seed += tm.ns(0, 1);
+        st->ns_traverse += tm.ns(1, 2);
+        st->ns_basecase += tm.ns(2, 3);
+        st->ns_fallback += tm.ns(3, 4);
     }
     return DTREE_OK;
 }
 
-}  // namespace
+// Shared option checks of dtree_knn and dtree_knn_batch.
+struct KnnOpts {
+    int prec, qb, seed_pts, spin;
+};
 
-int knn_entry(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_idx,
-              float* out_dist, const dtree_opts* o, void* stream, dtree_stats* st,
-              const ScratchArena* arena) {
-    if (st) memset(st, 0, sizeof(*st));
+int parse_opts(const dtree_opts* o, KnnOpts* ko) {
+    if (o)
+        for (int i = 0; i < 10; ++i)
+            if (o->reserved[i]) return DTREE_ERR_INVALID_ARG;
+    ko->prec = o ? o->precision : DTREE_PREC_FP32;
+    if (ko->prec < DTREE_PREC_FP32 || ko->prec > DTREE_PREC_BF16) return DTREE_ERR_INVALID_ARG;
+    ko->qb = (o && o->query_block) ? o->query_block : 128;
+    if (ko->qb < 16 || ko->qb > 128) return DTREE_ERR_INVALID_ARG;
+    if (o && o->proposal) return DTREE_ERR_NOT_TRAINED;
+    ko->seed_pts = (o && o->seed_points > 0) ? o->seed_points : 512;
+    ko->spin = (o && o->spin_budget > 0) ? o->spin_budget : (1 << 20);
+    return DTREE_OK;
+}
+
+int check_problem(const dtree_t* query, const dtree_t* ref, int32_t k, const int64_t* out_idx,
+                  const float* out_dist, HostProb* hp) {
     if (!ref) return DTREE_ERR_INVALID_ARG;
     const bool mono = query == nullptr || query == ref;
     const dtree_t* tq = mono ? ref : query;
     const int64_t m = ref->n;
     if (k <= 0 || (mono ? (int64_t)k > m - 1 : (int64_t)k >= m)) return DTREE_ERR_INVALID_K;
     if (!out_idx || !out_dist || tq->d != ref->d) return DTREE_ERR_INVALID_ARG;
-    if (o)
-        for (int i = 0; i < 10; ++i)
-            if (o->reserved[i]) return DTREE_ERR_INVALID_ARG;
-    const int prec = o ? o->precision : DTREE_PREC_FP32;
-    if (prec < DTREE_PREC_FP32 || prec > DTREE_PREC_BF16) return DTREE_ERR_INVALID_ARG;
-    int qb = (o && o->query_block) ? o->query_block : 128;
-    if (qb < 16 || qb > 128) return DTREE_ERR_INVALID_ARG;
-    if (o && o->proposal) return DTREE_ERR_NOT_TRAINED;
-    int seed = std::max<int>(k + 1, (o && o->seed_points > 0) ? o->seed_points : 512);
-    int spin = (o && o->spin_budget > 0) ? o->spin_budget : (1 << 20);
-    cudaStream_t s = (cudaStream_t)stream;
+    hp->tq = tq;
+    hp->tr = ref;
+    hp->mono = mono;
+    hp->k = k;
+    hp->out_idx = const_cast<int64_t*>(out_idx);
+    hp->out_dist = const_cast<float*>(out_dist);
+    hp->qb = 0;
+    return DTREE_OK;
+}
+
+int run_group(int dp, const HostProb* hp, int np, const KnnOpts& ko, cudaStream_t s,
+              dtree_stats* st, const ScratchArena* arena) {
+    switch (dp) {
+        case 4: return knn_batch_impl<4>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, s, st, arena);
+        case 8: return knn_batch_impl<8>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, s, st, arena);
+        case 16: return knn_batch_impl<16>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, s, st, arena);
+        case 32: return knn_batch_impl<32>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, s, st, arena);
+        default: return knn_batch_impl<64>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, s, st, arena);
+    }
+}
+
+int device_checks(int prec, bool arena, const HostProb* hp, int np, int* dev_out) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (arena) {
-        if (ref->device != dev || tq->device != dev) return DTREE_ERR_INVALID_ARG;
+        for (int i = 0; i < np; ++i)
+            if (hp[i].tr->device != dev || hp[i].tq->device != dev) return DTREE_ERR_INVALID_ARG;
     } else {
         prepare_pool(dev);
     }
@@ -690,14 +904,27 @@ int knn_entry(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_
         cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
         if (major != 10 || minor != 3) return DTREE_ERR_UNSUPPORTED;
     }
-    int rc;
-    switch (ref->dp) {
-        case 4: rc = knn_impl<4>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st, arena); break;
-        case 8: rc = knn_impl<8>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st, arena); break;
-        case 16: rc = knn_impl<16>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st, arena); break;
-        case 32: rc = knn_impl<32>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st, arena); break;
-        default: rc = knn_impl<64>(tq, ref, mono, k, out_idx, out_dist, qb, seed, prec, spin, s, st, arena); break;
-    }
+    *dev_out = dev;
+    return DTREE_OK;
+}
+
+}  // namespace
+
+int knn_entry(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_idx,
+              float* out_dist, const dtree_opts* o, void* stream, dtree_stats* st,
+              const ScratchArena* arena) {
+    if (st) memset(st, 0, sizeof(*st));
+    HostProb hp;
+    int rc = check_problem(query, ref, k, out_idx, out_dist, &hp);
+    if (rc != DTREE_OK) return rc;
+    KnnOpts ko;
+    rc = parse_opts(o, &ko);
+    if (rc != DTREE_OK) return rc;
+    int dev = 0;
+    rc = device_checks(ko.prec, arena != nullptr, &hp, 1, &dev);
+    if (rc != DTREE_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = run_group(ref->dp, &hp, 1, ko, s, st, arena);
     if (rc != DTREE_OK) cudaStreamSynchronize(s);
     return rc;
 }
@@ -707,4 +934,40 @@ int knn_entry(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_
 extern "C" int dtree_knn(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_idx,
                          float* out_dist, const dtree_opts* o, void* stream, dtree_stats* st) {
     return dt::knn_entry(query, ref, k, out_idx, out_dist, o, stream, st, nullptr);
+}
+
+extern "C" int dtree_knn_batch(int32_t nprob, const dtree_problem* probs, const dtree_opts* o,
+                               void* stream, dtree_stats* st) {
+    if (st) memset(st, 0, sizeof(*st));
+    if (nprob < 0 || (nprob > 0 && !probs)) return DTREE_ERR_INVALID_ARG;
+    if (nprob == 0) return DTREE_OK;
+    dt::KnnOpts ko;
+    int rc = dt::parse_opts(o, &ko);
+    if (rc != DTREE_OK) return rc;
+    std::vector<dt::HostProb> hp(nprob);
+    for (int i = 0; i < nprob; ++i) {
+        const int qb = probs[i].query_block;
+        if (qb != 0 && (qb < 16 || qb > 128)) return DTREE_ERR_INVALID_ARG;
+        rc = dt::check_problem(probs[i].query, probs[i].ref, probs[i].k, probs[i].out_idx,
+                               probs[i].out_dist, &hp[i]);
+        if (rc != DTREE_OK) return rc;
+        hp[i].qb = qb;
+    }
+    int dev = 0;
+    rc = dt::device_checks(ko.prec, false, hp.data(), nprob, &dev);
+    if (rc != DTREE_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    // one batched search per padded dimension (the kernels are built per width)
+    for (int dp : {4, 8, 16, 32, 64}) {
+        std::vector<dt::HostProb> group;
+        for (const auto& h : hp)
+            if (h.tr->dp == dp) group.push_back(h);
+        if (group.empty()) continue;
+        rc = dt::run_group(dp, group.data(), (int)group.size(), ko, s, st, nullptr);
+        if (rc != DTREE_OK) {
+            cudaStreamSynchronize(s);
+            return rc;
+        }
+    }
+    return DTREE_OK;
 }

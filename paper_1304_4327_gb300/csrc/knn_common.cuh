@@ -28,7 +28,13 @@ enum TileMode {
 constexpr int kQB = 128;           // queries of one work item (one thread each)
 constexpr int kEmptyIdx = 0x7fffffff;
 
-struct TileArgs {
+// One kNN problem of a batch, as the kernels see it.  Blocks (query-tree
+// nodes at the block level) are numbered across the batch: the problem's
+// blocks are [block0, block0 + nblocks).  Its queries occupy rows
+// [q0, q0 + n_query) of the per-query arrays (candidate lists, bounds), in
+// query-tree order, and its query nodes of levels 0..Lb occupy entries
+// [node0, node0 + 2^(Lb+1) - 1) of the per-node bound arrays.
+struct ProbDev {
     // query tree
     const float* qpts;
     const int32_t* qidx;
@@ -36,38 +42,50 @@ struct TileArgs {
     const int32_t* qcnt;
     const float* qlam;
     const float* qbox;  // nodes x 2 x DP (the block's box gives the tensor-core centring point)
-    int64_t qblock0;  // heap id of the first query block
-    int64_t nq;       // queries (rows of the candidate lists)
-    int cpb;          // work items (chunks of <= 128 queries) per block
     // reference tree
     const float* rpts;
     const int32_t* ridx;
     const int32_t* rbeg;
     const int32_t* rcnt;
-    const float* rbox;  // nodes x 2 x DP
+    const float* rbox;
+    // outputs, rows in the caller's query order
+    int64_t* out_idx;
+    float* out_dist;
+    int64_t qblock0;  // heap id of the first query block in the query tree
     int64_t rleaf0;   // heap id of reference leaf 0
+    int64_t q0;       // first row of the problem in the per-query arrays
+    int64_t node0;    // first entry of the problem in the per-node arrays
+    int32_t block0;   // first block of the problem
+    int32_t nblocks;
+    int32_t cpb;      // work items (chunks of <= 128 queries) per block
     int32_t k;
     int32_t mono;
+    int32_t Lb;       // level of the query blocks
+    int32_t hr;       // height of the reference tree
+    int32_t Ls;       // level of the seed subtrees in the reference tree
+    int32_t item0;    // first work item of the problem
+};
+
+struct TileArgs {
+    const ProbDev* probs;       // the batch's problems
+    const int32_t* blk_prob;    // per block: its problem
+    const int2* items;          // per work item: (block, chunk of 128 queries)
+    int nitems;
+    int64_t nq_all;             // rows of the per-query arrays (all problems' queries)
     // candidates
     const int32_t* seed_leaf0;  // per block: first seed leaf
     const int32_t* seed_nleaf;  // per block: seed leaves
-    const int64_t* csr_off;     // per block: [off[b], off[b+1]) in csr_leaf / csr_dmin
+    const int64_t* csr_off;     // per block: [off[b], off[b+1]) in csr_leaf / csr_dmin, in
+                                //   evaluation order (windows sorted by box-centre distance)
     const int32_t* csr_leaf;
     const float* csr_dmin;
-    const float* csr_key;       // evaluation order: distance between block and leaf box centres
-    const float* Bq;            // per block: B of the block from the traversal (or null)
-    // approximate candidate lists, [kc_rows][nq] layout
+    const float* Bn;            // per query node: B from the bounds pass (or null)
+    // approximate candidate lists, [kc_rows][nq_all] layout
     int kc_rows;
     float* cand_d;
     int32_t* cand_i;
     float* qub;                 // per query: upper bound on its true k-th distance (seed pass)
-    // work: blocks to process (null = all nblocks)
-    const int32_t* work_blocks;
-    int nwork;
     int* work_ctr;
-    // outputs
-    int64_t* out_idx;
-    float* out_dist;
     int4* fbq_list;    // queries whose error band overflowed: (tree position, block, ub bits, 0)
     int* fbq_count;
     int4* fbq2_list;   // of those, queries whose float32 band overflowed too
@@ -85,15 +103,17 @@ template <int DP>
 int launch_tile_tc(const TileArgs& a, int fmt, int kc, int mode, int items, int* err, int spin,
                    cudaStream_t s);
 
+// The traversal's frontier holds (global query node, reference node) pairs;
+// node_prob gives each global query node's problem.
 template <int DP>
-int launch_expand(const float* qbox, const float* rbox, const float* Bq, const int2* fin,
+int launch_expand(const ProbDev* probs, const int32_t* node_prob, const float* Bn, const int2* fin,
                   const int* nin, int2* fout, int* nout, int64_t cap, int4* outp, int* nout_p,
-                  int64_t cap_p, int* bcount, int Lb, int hr, int64_t qblock0, int64_t rleaf0,
-                  const int32_t* seed_leaf0, const int32_t* seed_nleaf, int* overflow,
-                  unsigned long long* stats, int grid, cudaStream_t s);
+                  int64_t cap_p, int* bcount, const int32_t* seed_leaf0,
+                  const int32_t* seed_nleaf, int* overflow, unsigned long long* stats, int np,
+                  int grid, cudaStream_t s);
 
 template <int DP>
-int launch_seed(const float* qbox, const float* rbox, int64_t qblock0, int nblocks, int Ls, int hr,
+int launch_seed(const ProbDev* probs, const int32_t* blk_prob, int nblocks,
                 int32_t* seed_leaf0, int32_t* seed_nleaf, cudaStream_t s);
 
 int occupancy_grid(const void* kernel, int threads, size_t smem);

@@ -236,50 +236,28 @@ static_assert(TT_N <= 32, "the diagnostic timer buffer holds 32 counters");
 // Named barriers of the pipelined kernel (0 is __syncthreads).
 enum { BAR_EPI = 1, BAR_CONV = 2, BAR_G0 = 3 };
 
-// The planner warp: read the window's candidates (row range, d_min and order
-// key) into shared memory, sorting them by the order key (the distance
-// between the block's and the leaf's box centres) in MODE_MAIN.
+// The planner warp: read the window's candidates (row range and d_min) into
+// shared memory, in list order (a block's list is sorted nearest-first).
 template <int NC, int MODE>
-__device__ __forceinline__ void load_window(const TileArgs& a, int64_t w0, int wn, int nseed,
-                                            int sleaf0, int64_t c0, uint64_t* skey, int4* srow) {
+__device__ __forceinline__ void load_window(const TileArgs& a, const ProbDev& P, int64_t w0,
+                                            int wn, int nseed, int sleaf0, int64_t c0,
+                                            uint64_t* skey, int4* srow) {
     const int lane = threadIdx.x & 31;
     for (int i = lane; i < wn; i += 32) {
         const int64_t ci = w0 + i;
         int leaf;
-        float dmin = 0.f, ord = 0.f;
+        float dmin = 0.f;
         if (ci < nseed) {
             leaf = sleaf0 + (int)ci;
         } else {
             leaf = a.csr_leaf[c0 + ci - nseed];
             dmin = a.csr_dmin[c0 + ci - nseed];
-            ord = a.csr_key[c0 + ci - nseed];
         }
-        const int64_t ln = a.rleaf0 + leaf;
-        srow[i] = make_int4(a.rbeg[ln], a.rcnt[ln], __float_as_int(dmin), 0);
-        skey[i] = ((uint64_t)f2o(ord) << 32) | (uint32_t)i;
+        const int64_t ln = P.rleaf0 + leaf;
+        srow[i] = make_int4(P.rbeg[ln], P.rcnt[ln], __float_as_int(dmin), 0);
+        skey[i] = (uint64_t)i;
     }
-    if (MODE != MODE_MAIN) {
-        __syncwarp();
-        return;
-    }
-    int np2 = 1;
-    while (np2 < wn) np2 <<= 1;
-    for (int i = wn + lane; i < np2; i += 32) skey[i] = ~0ull;
     __syncwarp();
-    for (int kk = 2; kk <= np2; kk <<= 1)
-        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-            for (int t = lane; t < np2 / 2; t += 32) {
-                int i = 2 * t - (t & (jj - 1));
-                int l = i + jj;
-                bool up = (i & kk) == 0;
-                uint64_t x = skey[i], y = skey[l];
-                if ((x > y) == up) {
-                    skey[i] = y;
-                    skey[l] = x;
-                }
-            }
-            __syncwarp();
-        }
 }
 
 // One CTA per SM, 12 warps:
@@ -318,13 +296,14 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
     __shared__ int smeta[NS], srmeta[NR];
     __shared__ uint32_t s_tmem;
     __shared__ int s_item;
+    __shared__ ProbDev s_prob;
     __shared__ volatile int s_fail, s_cmeta;
     __shared__ volatile float s_wmax[8], s_wmin[8];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int role = warp < 4 ? 0 : warp < 8 ? 1 : warp == 8 ? 2 : 3;
     const int qt = tid & 127;  // query row of an epilogue thread
-    const int nitems = a.nwork * a.cpb;
+    const int nitems = a.nitems;
     unsigned long long n_skip = 0, n_eval = 0, n_pp = 0, n_re = 0, n_ins = 0;
 
     if (tid == 0) {
@@ -350,26 +329,32 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
     uint32_t ctile = role;  // epilogue group: next operand slot use of this group
     int last_slot = -1;
 
+    const ProbDev& P = s_prob;
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(a.work_ctr, 1);
+        if (tid == 0) {
+            s_item = atomicAdd(a.work_ctr, 1);
+            if (s_item < nitems) s_prob = a.probs[a.blk_prob[a.items[s_item].x]];
+        }
         __syncthreads();
         const int item = s_item;
         if (item >= nitems || s_fail) break;
-        const int wb = item / a.cpb, chunk = item - wb * a.cpb;
-        const int blk = a.work_blocks ? a.work_blocks[wb] : wb;
-        const int64_t qnode = a.qblock0 + blk;
-        const int nq = min(kQB, a.qcnt[qnode] - chunk * kQB);
+        const int2 wi = a.items[item];
+        const int blk = wi.x, chunk = wi.y;  // global block, chunk of its queries
+        const int64_t qnode = P.qblock0 + (blk - P.block0);
+        const int nq = min(kQB, P.qcnt[qnode] - chunk * kQB);
         if (nq <= 0) {
             __syncthreads();
             continue;
         }
         long long tm0 = clock64();
-        const float* bx = a.qbox + qnode * 2 * DP;
+        const float* bx = P.qbox + qnode * 2 * DP;
         if (tid < DP) scen[tid] = 0.5f * (bx[tid] + bx[DP + tid]);
         __syncthreads();
         const bool act = role < 2 && qt < nq;
-        const int myq = a.qbeg[qnode] + chunk * kQB + qt;
-        const float lam2 = 2.f * a.qlam[qnode];
+        const int myq = P.qbeg[qnode] + chunk * kQB + qt;
+        const int kq = P.k;  // read once: stores below could alias P
+        const bool mono = P.mono != 0;
+        const float lam2 = 2.f * P.qlam[qnode];
         float qa = 0.f, qn = 0.f;
         float ld[KC];
         int li[KC];
@@ -377,7 +362,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
             // the query, centred and rounded (group 0 writes row qt of the A tile)
             float qa2 = 0.f;
             float h[DP], xh[DP], xl[DP];
-            const float4* q4 = reinterpret_cast<const float4*>(a.qpts + (int64_t)myq * DP);
+            const float4* q4 = reinterpret_cast<const float4*>(P.qpts + (int64_t)myq * DP);
 #pragma unroll
             for (int j = 0; j < DP / 4; ++j) {
                 float4 v = act ? q4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -404,11 +389,11 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                 ld[j] = INFINITY;
                 li[j] = kEmptyIdx;
                 if (MODE == MODE_MAIN && act) {
-                    ld[j] = a.cand_d[(int64_t)j * a.nq + myq];
-                    li[j] = a.cand_i[(int64_t)j * a.nq + myq];
+                    ld[j] = a.cand_d[(int64_t)j * a.nq_all + (P.q0 + myq)];
+                    li[j] = a.cand_i[(int64_t)j * a.nq_all + (P.q0 + myq)];
                 }
             }
-            float ub = Bd::ub(list_at(ld, a.k - 1), qa);
+            float ub = Bd::ub(list_at(ld, kq - 1), qa);
             float vmax = act ? ub : -INFINITY, vmin = act ? ub : INFINITY;
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
@@ -429,7 +414,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
 
         if (role == 2) {
             // ================= planner (warp 8) =================
-            const float Bq = a.Bq ? a.Bq[blk] : INFINITY;
+            const float Bq = a.Bn ? a.Bn[P.node0 + qnode] : INFINITY;
             const int nseed = MODE == MODE_MAIN ? 0 : a.seed_nleaf[blk];
             const int sleaf0 = MODE == MODE_MAIN ? 0 : a.seed_leaf0[blk];
             const int64_t c0 = MODE == MODE_SEED ? 0 : a.csr_off[blk];
@@ -439,7 +424,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
             for (int64_t w0 = 0; w0 < ntot && !fail; w0 += S::SORTCAP) {
                 const int wn = (int)(ntot - w0 < S::SORTCAP ? ntot - w0 : S::SORTCAP);
                 long long t0 = clock64();
-                load_window<S::SORTCAP, MODE>(a, w0, wn, nseed, sleaf0, c0, skey, srow);
+                load_window<S::SORTCAP, MODE>(a, P, w0, wn, nseed, sleaf0, c0, skey, srow);
                 if (x.timers && lane == 0)
                     atomicAdd(&x.timers[TT_PLAN_WINDOW], (unsigned long long)(clock64() - t0));
                 int cur = 0, part = 0;
@@ -517,7 +502,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                         }
                         __syncwarp();
                         if (put) {
-                            tc::bulk_g2s(raw + (nst + excl) * DP, a.rpts + (int64_t)lb * DP,
+                            tc::bulk_g2s(raw + (nst + excl) * DP, P.rpts + (int64_t)lb * DP,
                                          (uint32_t)take * DP * 4, &raw_full[r]);
                             for (int i = 0; i < take; ++i) rpos[nst + excl + i] = lb + i;
                         }
@@ -707,7 +692,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                     // inside the error band of the current k-th key (a key above
                     // the band can never be a true k-nearest neighbour)
                     auto threshold = [&]() {
-                        const float bnd = Bd::band(Bd::ub(list_at(ld, a.k - 1), qa), qa);
+                        const float bnd = Bd::band(Bd::ub(list_at(ld, kq - 1), qa), qa);
                         return __fsub_ru(fminf(ld[KC - 1], bnd), qn);
                     };
                     float t = threshold();
@@ -721,10 +706,10 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                         for (int e = 0; e < nb; ++e) {
                             const float sv = qn + bw[e * kQB];
                             const int rp = bi[e * kQB];
-                            if (key_less(sv, rp, ld[KC - 1], li[KC - 1]) && !(a.mono && rp == myq)) {
+                            if (key_less(sv, rp, ld[KC - 1], li[KC - 1]) && !(mono && rp == myq)) {
                                 // the band moves only when the k-th key does
-                                const bool kth_moves = key_less(sv, rp, list_at(ld, a.k - 1),
-                                                                list_at(li, a.k - 1));
+                                const bool kth_moves = key_less(sv, rp, list_at(ld, kq - 1),
+                                                                list_at(li, kq - 1));
                                 list_insert_par(ld, li, sv, rp);
                                 t = kth_moves ? threshold() : fminf(t, __fsub_ru(ld[KC - 1], qn));
                                 changed = true;
@@ -802,7 +787,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                 if (nst < 0) break;
                 if (!__any_sync(0xffffffffu, changed)) continue;  // the published bound stands
                 long long tb0 = clock64();
-                float ub = Bd::ub(list_at(ld, a.k - 1), qa);
+                float ub = Bd::ub(list_at(ld, kq - 1), qa);
                 float vmax = act ? ub : -INFINITY, vmin = act ? ub : INFINITY;
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) {
@@ -844,13 +829,13 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                     if (act) {
 #pragma unroll
                         for (int j = 0; j < KC; ++j) {
-                            a.cand_d[(int64_t)j * a.nq + myq] = ld[j];
-                            a.cand_i[(int64_t)j * a.nq + myq] = li[j];
+                            a.cand_d[(int64_t)j * a.nq_all + (P.q0 + myq)] = ld[j];
+                            a.cand_i[(int64_t)j * a.nq_all + (P.q0 + myq)] = li[j];
                         }
-                        a.qub[myq] = Bd::ub(list_at(ld, a.k - 1), qa);
+                        a.qub[P.q0 + myq] = Bd::ub(list_at(ld, kq - 1), qa);
                     }
                 } else {
-                    const float ubk = Bd::ub(list_at(ld, a.k - 1), qa);
+                    const float ubk = Bd::ub(list_at(ld, kq - 1), qa);
                     const float band = Bd::band(ubk, qa);
                     const bool ovf = act && li[KC - 1] != kEmptyIdx && !(ld[KC - 1] > band);
                     // the re-rank below reuses the merge buffers: all of group 0 has read them
@@ -862,19 +847,19 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                         // float64 re-rank of the band candidates in shared memory
                         double* rd = reinterpret_cast<double*>(smem + L::OFF_RAW);
                         int32_t* ri = reinterpret_cast<int32_t*>(smem + L::OFF_KEY);
-                        const float* qp = a.qpts + (int64_t)myq * DP;
+                        const float* qp = P.qpts + (int64_t)myq * DP;
                         int nb = 0;
 #pragma unroll
                         for (int j = 0; j < KC; ++j) {
                             if (li[j] != kEmptyIdx && !(ld[j] > band)) {
-                                rd[nb * kQB + qt] = exact_d2<DP>(qp, a.rpts + (int64_t)li[j] * DP);
-                                ri[nb * kQB + qt] = a.ridx[li[j]];
+                                rd[nb * kQB + qt] = exact_d2<DP>(qp, P.rpts + (int64_t)li[j] * DP);
+                                ri[nb * kQB + qt] = P.ridx[li[j]];
                                 ++nb;
                             }
                         }
                         n_re += nb;
-                        const int64_t base = (int64_t)a.qidx[myq] * a.k;
-                        for (int j = 0; j < a.k; ++j) {
+                        const int64_t base = (int64_t)P.qidx[myq] * kq;
+                        for (int j = 0; j < kq; ++j) {
                             int best = j;
                             for (int c = j + 1; c < nb; ++c)
                                 if (key_less(rd[c * kQB + qt], ri[c * kQB + qt], rd[best * kQB + qt],
@@ -884,8 +869,8 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                             const int bi = ri[best * kQB + qt];
                             rd[best * kQB + qt] = rd[j * kQB + qt];
                             ri[best * kQB + qt] = ri[j * kQB + qt];
-                            a.out_idx[base + j] = bi;
-                            a.out_dist[base + j] = (float)sqrt(bd);
+                            P.out_idx[base + j] = bi;
+                            P.out_dist[base + j] = (float)sqrt(bd);
                         }
                     }
                 }

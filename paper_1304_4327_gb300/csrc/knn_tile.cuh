@@ -106,7 +106,7 @@ __device__ __forceinline__ float ub_of(T kth) {
 // part of a leaf that fits) into a stage of at most TN points.  stab gets one
 // (first row, rows, stage offset) entry per run of rows.
 template <int TN, int MODE>
-__device__ __forceinline__ void stage_fill(const TileArgs& a, const uint64_t* scand, int64_t w0,
+__device__ __forceinline__ void stage_fill(const TileArgs& a, const ProbDev& P, int64_t w0,
                                            int wn, int nseed, int sleaf0, int64_t c0, int3* stab,
                                            unsigned long long& n_skip, unsigned long long& n_eval,
                                            int& s_cur, int& s_part, int& s_nst, int& s_ntab,
@@ -119,8 +119,8 @@ __device__ __forceinline__ void stage_fill(const TileArgs& a, const uint64_t* sc
         int leaf = 0;
         float dmin = 0.f;
         if (valid) {
-            if (MODE == MODE_MAIN) {
-                const int64_t ci = c0 + w0 + (uint32_t)scand[c];
+            if (MODE == MODE_MAIN) {  // the block's candidates, sorted nearest-first
+                const int64_t ci = c0 + w0 + c;
                 leaf = a.csr_leaf[ci];
                 dmin = a.csr_dmin[ci];
             } else {
@@ -136,9 +136,9 @@ __device__ __forceinline__ void stage_fill(const TileArgs& a, const uint64_t* sc
         bool keep = valid && !(dmin > Bc);
         int lb = 0, lc = 0;
         if (keep) {
-            int64_t ln = a.rleaf0 + leaf;
-            lb = a.rbeg[ln];
-            lc = a.rcnt[ln];
+            int64_t ln = P.rleaf0 + leaf;
+            lb = P.rbeg[ln];
+            lc = P.rcnt[ln];
         }
         if (lane == 0 && part > 0 && keep) {  // rest of a split leaf
             lb += part;
@@ -187,72 +187,44 @@ __device__ __forceinline__ void stage_fill(const TileArgs& a, const uint64_t* sc
     }
 }
 
-__device__ __forceinline__ void group_sync(int bar, int n) {
-    if (bar == 0) __syncthreads();
-    else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(n) : "memory");
-}
-
-// Sort the window [w0, w0 + wn) of a block's candidate list by its order key
-// (window index in the low bits) into scand: bitonic sort by the NT threads of a group
-// (thread index tid within it, barrier BAR; 0 = the whole CTA).
-template <int NT, int BAR = 0>
-__device__ __forceinline__ void sort_window(const TileArgs& a, int64_t c0, int64_t w0, int wn,
-                                            uint64_t* scand, int tid = threadIdx.x) {
-    int np2 = 1;
-    while (np2 < wn) np2 <<= 1;
-    for (int i = tid; i < np2; i += NT) {
-        uint64_t key = ~0ull;
-        if (i < wn) key = ((uint64_t)f2o(a.csr_key[c0 + w0 + i]) << 32) | (uint32_t)i;
-        scand[i] = key;
-    }
-    group_sync(BAR, NT);
-    for (int kk = 2; kk <= np2; kk <<= 1)
-        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-            for (int t = tid; t < np2 / 2; t += NT) {
-                int i = 2 * t - (t & (jj - 1));
-                int l = i + jj;
-                bool up = (i & kk) == 0;
-                uint64_t x = scand[i], y = scand[l];
-                if ((x > y) == up) {
-                    scand[i] = y;
-                    scand[l] = x;
-                }
-            }
-            group_sync(BAR, NT);
-        }
-}
-
 template <typename T, int DP, int KC, int MODE>
 __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
     constexpr int TN = 4096 / DP;       // staged reference points (16 KB)
-    constexpr int SORTCAP = 2048;       // candidates sorted per window
+    constexpr int WINDOW = 2048;        // candidates per window of the main pass
     __shared__ __align__(16) float rs[TN * DP];
     __shared__ int32_t spos[TN];
-    __shared__ uint64_t scand[MODE == MODE_MAIN ? SORTCAP : 1];
     __shared__ int3 stab[TN];
     __shared__ int s_item, s_ntab, s_nst, s_cur, s_part;
     __shared__ float s_B;
     __shared__ float s_rmax[kQB / 32], s_rmin[kQB / 32];
+    __shared__ ProbDev s_prob;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nitems = a.nwork * a.cpb;
+    const int nitems = a.nitems;
     unsigned long long n_skip = 0, n_eval = 0, n_pp = 0, n_re = 0;
+    const ProbDev& P = s_prob;
 
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(a.work_ctr, 1);
+        if (tid == 0) {
+            s_item = atomicAdd(a.work_ctr, 1);
+            if (s_item < nitems) s_prob = a.probs[a.blk_prob[a.items[s_item].x]];
+        }
         __syncthreads();
         const int item = s_item;
         if (item >= nitems) break;
-        const int wb = item / a.cpb, chunk = item - wb * a.cpb;
-        const int blk = a.work_blocks ? a.work_blocks[wb] : wb;
-        const int64_t qnode = a.qblock0 + blk;
-        const int nq = min(kQB, a.qcnt[qnode] - chunk * kQB);
+        const int2 wi = a.items[item];
+        const int blk = wi.x, chunk = wi.y;  // global block, chunk of its queries
+        const int64_t qnode = P.qblock0 + (blk - P.block0);
+        const int nq = min(kQB, P.qcnt[qnode] - chunk * kQB);
         if (nq > 0) {
             const bool act = tid < nq;
-            const int myq = a.qbeg[qnode] + chunk * kQB + tid;
+            const int myq = P.qbeg[qnode] + chunk * kQB + tid;
+            const int64_t row = P.q0 + myq;  // the query's row in the per-query arrays
+            const int kq = P.k;                // read once: stores below could alias P
+            const bool mono = P.mono != 0;
             float q[DP];
             {
-                const float4* q4 = reinterpret_cast<const float4*>(a.qpts + (int64_t)myq * DP);
+                const float4* q4 = reinterpret_cast<const float4*>(P.qpts + (int64_t)myq * DP);
 #pragma unroll
                 for (int j = 0; j < DP / 4; ++j) {
                     float4 v = act ? q4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -269,16 +241,16 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
                 ld[j] = (T)INFINITY;
                 li[j] = kEmptyIdx;
                 if (MODE == MODE_MAIN && act) {
-                    ld[j] = (T)a.cand_d[(int64_t)j * a.nq + myq];
-                    li[j] = a.cand_i[(int64_t)j * a.nq + myq];
+                    ld[j] = (T)a.cand_d[(int64_t)j * a.nq_all + row];
+                    li[j] = a.cand_i[(int64_t)j * a.nq_all + row];
                 }
             }
-            const float lam2 = 2.f * a.qlam[qnode];
-            const float Bq = a.Bq ? a.Bq[blk] : INFINITY;
+            const float lam2 = 2.f * P.qlam[qnode];
+            const float Bq = a.Bn ? a.Bn[P.node0 + qnode] : INFINITY;
 
             // the block's live bound: min(B from the traversal, B_1, B_2)
             auto refresh_bound = [&]() {
-                float ub = ub_of<T, DP>(list_at(ld, a.k - 1));
+                float ub = ub_of<T, DP>(list_at(ld, kq - 1));
                 float vmax = act ? ub : -INFINITY, vmin = act ? ub : INFINITY;
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) {
@@ -307,11 +279,10 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
             const int64_t c0 = MODE == MODE_SEED ? 0 : a.csr_off[blk];
             const int64_t c1 = MODE == MODE_SEED ? 0 : a.csr_off[blk + 1];
             const int64_t ntot = nseed + (c1 - c0);
-            const int64_t win = MODE == MODE_MAIN ? SORTCAP : (ntot > 0 ? ntot : 1);
+            const int64_t win = MODE == MODE_MAIN ? WINDOW : (ntot > 0 ? ntot : 1);
 
             for (int64_t w0 = 0; w0 < ntot; w0 += win) {
                 const int wn = (int)(ntot - w0 < win ? ntot - w0 : win);
-                if (MODE == MODE_MAIN) sort_window<kQB>(a, c0, w0, wn, scand);
                 if (tid == 0) {
                     s_cur = 0;
                     s_part = 0;
@@ -320,14 +291,14 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
                 while (s_cur < wn) {
                     // ---- warp 0 fills the stage with whole or partial leaves
                     if (warp == 0)
-                        stage_fill<TN, MODE>(a, scand, w0, wn, nseed, sleaf0, c0, stab, n_skip,
+                        stage_fill<TN, MODE>(a, P, w0, wn, nseed, sleaf0, c0, stab, n_skip,
                                              n_eval, s_cur, s_part, s_nst, s_ntab, s_B);
                     __syncthreads();
                     // ---- all warps copy the staged rows
                     const int ntab = s_ntab, nst = s_nst;
                     for (int t = warp; t < ntab; t += kQB / 32) {
                         int3 e = stab[t];
-                        const float4* src = reinterpret_cast<const float4*>(a.rpts) + (int64_t)e.x * (DP / 4);
+                        const float4* src = reinterpret_cast<const float4*>(P.rpts) + (int64_t)e.x * (DP / 4);
                         float4* dst = reinterpret_cast<float4*>(rs) + e.z * (DP / 4);
                         for (int f = lane; f < e.y * (DP / 4); f += 32) dst[f] = src[f];
                         for (int i = lane; i < e.y; i += 32) {
@@ -366,7 +337,7 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
                             }
                             const int rp = spos[e];
                             const int tie = rp;
-                            if (key_less(acc, tie, ld[KC - 1], li[KC - 1]) && !(a.mono && rp == myq))
+                            if (key_less(acc, tie, ld[KC - 1], li[KC - 1]) && !(mono && rp == myq))
                                 list_insert(ld, li, acc, tie);
                         }
                     }
@@ -381,23 +352,23 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
                 if (act) {
 #pragma unroll
                     for (int j = 0; j < KC; ++j) {
-                        a.cand_d[(int64_t)j * a.nq + myq] = (float)ld[j];
-                        a.cand_i[(int64_t)j * a.nq + myq] = li[j];
+                        a.cand_d[(int64_t)j * a.nq_all + row] = (float)ld[j];
+                        a.cand_i[(int64_t)j * a.nq_all + row] = li[j];
                     }
                     // the main pass may keep longer lists: their other rows start empty
                     for (int j = KC; j < a.kc_rows; ++j) {
-                        a.cand_d[(int64_t)j * a.nq + myq] = INFINITY;
-                        a.cand_i[(int64_t)j * a.nq + myq] = kEmptyIdx;
+                        a.cand_d[(int64_t)j * a.nq_all + row] = INFINITY;
+                        a.cand_i[(int64_t)j * a.nq_all + row] = kEmptyIdx;
                     }
-                    a.qub[myq] = ub_of<T, DP>(list_at(ld, a.k - 1));
+                    a.qub[row] = ub_of<T, DP>(list_at(ld, kq - 1));
                 }
             } else {
-                const float kth = (float)list_at(ld, a.k - 1);
+                const float kth = (float)list_at(ld, kq - 1);
                 const float band = __fmul_ru(kth, 1.f + 4.f * rel_eps<DP>());
                 const bool ovf = act && li[KC - 1] != kEmptyIdx && !((float)ld[KC - 1] > band);
                 if (ovf) {
                     a.fbq_list[atomicAdd(a.fbq_count, 1)] =
-                        make_int4(myq, blk, __float_as_int(ub_of<T, DP>(list_at(ld, a.k - 1))), 0);
+                        make_int4(myq, blk, __float_as_int(ub_of<T, DP>(list_at(ld, kq - 1))), 0);
                 } else if (act) {
                     double rd[KC];
                     int ri[KC];
@@ -410,7 +381,7 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
                     for (int j = 0; j < KC; ++j) {
                         if (li[j] != kEmptyIdx && !((float)ld[j] > band)) {
                             float r[DP];
-                            const float4* r4 = reinterpret_cast<const float4*>(a.rpts + (int64_t)li[j] * DP);
+                            const float4* r4 = reinterpret_cast<const float4*>(P.rpts + (int64_t)li[j] * DP);
 #pragma unroll
                             for (int u = 0; u < DP / 4; ++u) {
                                 float4 v = r4[u];
@@ -419,16 +390,16 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
                                 r[4 * u + 2] = v.z;
                                 r[4 * u + 3] = v.w;
                             }
-                            list_insert(rd, ri, exact_d2<DP>(q, r), a.ridx[li[j]]);
+                            list_insert(rd, ri, exact_d2<DP>(q, r), P.ridx[li[j]]);
                             ++n_re;
                         }
                     }
-                    int64_t base = (int64_t)a.qidx[myq] * a.k;
+                    int64_t base = (int64_t)P.qidx[myq] * kq;
 #pragma unroll
                     for (int j = 0; j < KC; ++j)
-                        if (j < a.k) {
-                            a.out_idx[base + j] = ri[j];
-                            a.out_dist[base + j] = (float)sqrt(rd[j]);
+                        if (j < kq) {
+                            P.out_idx[base + j] = ri[j];
+                            P.out_dist[base + j] = (float)sqrt(rd[j]);
                         }
                 }
             }
@@ -498,12 +469,15 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
     __shared__ double s_rd[KC];
     __shared__ int s_ri[KC];
     const int4 e = (EXACT ? a.fbq2_list : a.fbq_list)[blockIdx.x];
-    const int myq = e.x, blk = e.y;
+    const int myq = e.x, blk = e.y;  // query (tree position in its problem), global block
+    const ProbDev& P = a.probs[a.blk_prob[blk]];
+    const int kq = P.k;  // read once: stores below could alias P
+    const bool mono = P.mono != 0;
     const float ub = __int_as_float(e.z);
     const int tid = threadIdx.x;
     float q[DP];
     {
-        const float4* q4 = reinterpret_cast<const float4*>(a.qpts + (int64_t)myq * DP);
+        const float4* q4 = reinterpret_cast<const float4*>(P.qpts + (int64_t)myq * DP);
 #pragma unroll
         for (int j = 0; j < DP / 4; ++j) {
             float4 v = q4[j];
@@ -535,7 +509,7 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
             } else if (!(a.csr_dmin[c0 + c - nseed] > ub)) {
                 leaf = a.csr_leaf[c0 + c - nseed];
             }
-            if (leaf >= 0 && point_box_dmin_down<DP>(q, a.rbox + (a.rleaf0 + leaf) * 2 * DP) > ub)
+            if (leaf >= 0 && point_box_dmin_down<DP>(q, P.rbox + (P.rleaf0 + leaf) * 2 * DP) > ub)
                 leaf = -1;
         }
         if (leaf >= 0) s_lb[atomicAdd(&s_n, 1)] = leaf;
@@ -549,7 +523,7 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
                 int acc = 0;
                 for (int i = 0; i < nb; ++i) {
                     s_pre[i] = acc;
-                    acc += a.rcnt[a.rleaf0 + s_lb[i]];
+                    acc += P.rcnt[P.rleaf0 + s_lb[i]];
                 }
                 s_pre[nb] = acc;
             }
@@ -562,14 +536,14 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
                     if (s_pre[mid] <= p) lo = mid;
                     else hi = mid - 1;
                 }
-                const int r = a.rbeg[a.rleaf0 + s_lb[lo]] + (p - s_pre[lo]);
-                if (a.mono && r == myq) continue;
+                const int r = P.rbeg[P.rleaf0 + s_lb[lo]] + (p - s_pre[lo]);
+                if (mono && r == myq) continue;
                 if constexpr (EXACT) {
-                    const double d2 = exact_d2<DP>(q, a.rpts + (int64_t)r * DP);
-                    const int orig = a.ridx[r];
+                    const double d2 = exact_d2<DP>(q, P.rpts + (int64_t)r * DP);
+                    const int orig = P.ridx[r];
                     if (key_less(d2, orig, ld[KC - 1], li[KC - 1])) list_insert(ld, li, d2, orig);
                 } else {
-                    const float d2 = approx_d2<DP>(q, a.rpts + (int64_t)r * DP);
+                    const float d2 = approx_d2<DP>(q, P.rpts + (int64_t)r * DP);
                     if (key_less(d2, r, ld[KC - 1], li[KC - 1])) list_insert(ld, li, d2, r);
                 }
             }
@@ -584,8 +558,8 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
         mi[j * kQB + tid] = li[j];
     }
     __syncthreads();
-    const int64_t obase = (int64_t)a.qidx[myq] * a.k;
-    const int nout = EXACT ? a.k : KC;
+    const int64_t obase = (int64_t)P.qidx[myq] * kq;
+    const int nout = EXACT ? kq : KC;
     if (tid == 0) {
         // merge the 128 sorted lists: the first nout keys overall
         int head[kQB];
@@ -606,8 +580,8 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
             }
             head[best]++;
             if constexpr (EXACT) {
-                a.out_idx[obase + j] = bi;
-                a.out_dist[obase + j] = (float)sqrt(bd);
+                P.out_idx[obase + j] = bi;
+                P.out_dist[obase + j] = (float)sqrt(bd);
             } else {
                 s_fd[j] = bd;
                 s_fi[j] = bi;
@@ -616,7 +590,7 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
         if constexpr (!EXACT) {
             // every true k-nearest neighbour has a key <= band; the band must
             // end inside the list, else the float64 pass takes the query
-            const float band = __fmul_ru(s_fd[a.k - 1], 1.f + 4.f * rel_eps<DP>());
+            const float band = __fmul_ru(s_fd[kq - 1], 1.f + 4.f * rel_eps<DP>());
             int n = 0;
             while (n < KC && s_fi[n] != kEmptyIdx && !(s_fd[n] > band)) ++n;
             if (n == KC) {
@@ -631,8 +605,8 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
         const int n = s_nb;
         if (n < 0) return;  // uniform: the float64 pass recomputes this query
         if (tid < n) {
-            s_rd[tid] = exact_d2<DP>(q, a.rpts + (int64_t)s_fi[tid] * DP);
-            s_ri[tid] = a.ridx[s_fi[tid]];
+            s_rd[tid] = exact_d2<DP>(q, P.rpts + (int64_t)s_fi[tid] * DP);
+            s_ri[tid] = P.ridx[s_fi[tid]];
         }
         __syncthreads();
         if (tid == 0) {
@@ -644,9 +618,9 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
                 ri[j] = kEmptyIdx;
             }
             for (int j = 0; j < n; ++j) list_insert(rd, ri, s_rd[j], s_ri[j]);
-            for (int j = 0; j < a.k; ++j) {
-                a.out_idx[obase + j] = ri[j];
-                a.out_dist[obase + j] = (float)sqrt(rd[j]);
+            for (int j = 0; j < kq; ++j) {
+                P.out_idx[obase + j] = ri[j];
+                P.out_dist[obase + j] = (float)sqrt(rd[j]);
             }
         }
         if (tid == 0) atomicAdd(&a.stats[ST_RERANK], (unsigned long long)n);

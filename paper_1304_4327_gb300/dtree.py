@@ -38,6 +38,11 @@ class dtree_stats(ctypes.Structure):
     _fields_ = [(f, _I64) for f in STAT_FIELDS]
 
 
+class dtree_problem(ctypes.Structure):
+    _fields_ = [("query", _P), ("ref", _P), ("k", _I32), ("query_block", _I32),
+                ("out_idx", _P), ("out_dist", _P)]
+
+
 class DTreeError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -75,7 +80,10 @@ def _load() -> ctypes.CDLL:
     lib.dtree_alloc_count.argtypes = []
     lib.dtree_alloc_count.restype = _I64
     lib.dtree_knn_noalloc.argtypes = [_P, _P, _I32, _P, _P, ctypes.POINTER(dtree_opts), _P]
-    for f in (lib.dtree_build, lib.dtree_knn, lib.dtree_export, lib.dtree_knn_noalloc):
+    lib.dtree_knn_batch.argtypes = [_I32, ctypes.POINTER(dtree_problem), ctypes.POINTER(dtree_opts),
+                                    _P, ctypes.POINTER(dtree_stats)]
+    for f in (lib.dtree_build, lib.dtree_knn, lib.dtree_export, lib.dtree_knn_noalloc,
+              lib.dtree_knn_batch):
         f.restype = ctypes.c_int
     return lib
 
@@ -197,6 +205,44 @@ def dtree_knn(query: Optional[Tree], ref: Tree, k: int, precision: str = "fp32",
     if with_stats:
         return out_idx, out_dist, {f: int(getattr(st, f)) for f in STAT_FIELDS}
     return out_idx, out_dist
+
+
+def dtree_knn_batch(problems, precision: str = "fp32", query_block: int = 0,
+                    seed_points: int = 0, stream=None, with_stats: bool = False):
+    """Many independent kNN problems in one call.
+
+    ``problems``: a sequence of (query Tree or None, ref Tree, k) or
+    (query, ref, k, query_block).  Returns a list of (idx, dist) device
+    tensors, one pair per problem (plus a dict of counters summed over the
+    batch when ``with_stats``).
+    """
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = len(problems)
+    arr = (dtree_problem * max(n, 1))()
+    outs = []
+    for i, pr in enumerate(problems):
+        query, ref, k = pr[0], pr[1], int(pr[2])
+        qb = int(pr[3]) if len(pr) > 3 else 0
+        nq = ref.n if query is None else query.n
+        kk = max(k, 0)
+        oi = torch.empty((nq, kk), dtype=torch.int64, device=dev)
+        od = torch.empty((nq, kk), dtype=torch.float32, device=dev)
+        outs.append((oi, od))
+        arr[i].query = None if query is None else query.handle
+        arr[i].ref = ref.handle
+        arr[i].k = k
+        arr[i].query_block = qb
+        arr[i].out_idx = oi.data_ptr() if oi.numel() else None
+        arr[i].out_dist = od.data_ptr() if od.numel() else None
+    o = _opts(precision=PRECISIONS[precision], query_block=query_block, seed_points=seed_points)
+    st = dtree_stats()
+    rc = _lib.dtree_knn_batch(n, arr, ctypes.byref(o), _stream(stream),
+                              ctypes.byref(st) if with_stats else None)
+    if rc != DTREE_OK:
+        raise DTreeError(rc, "dtree_knn_batch")
+    if with_stats:
+        return outs, {f: int(getattr(st, f)) for f in STAT_FIELDS}
+    return outs
 
 
 NOALLOC_MAX_QUERIES = 65536
