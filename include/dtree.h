@@ -70,7 +70,9 @@ typedef struct dtree_opts {
                               (default 128) */
     int32_t seed_points;   /* dtree_knn: min reference points of the seed subtree evaluated
                               before the traversal (default 512) */
-    int32_t proposal;      /* dtree_knn: 1 = use the attached learned proposal (default 0) */
+    int32_t proposal;      /* dtree_knn: M > 0 evaluates each query block's top-M cells of the
+                              proposal attached to the reference tree (see
+                              dtree_attach_proposal) in the seed pass, M <= 8; 0: none */
     int32_t spin_budget;   /* dtree_knn: polls of a device-side wait before it gives up
                               with DTREE_ERR_TIMEOUT (default 1 << 20, about a second) */
     int32_t reserved[10];  /* must be zero */
@@ -222,6 +224,71 @@ int dtree_knn_batch(int32_t nprob, const dtree_problem* probs, const dtree_opts*
 #define DTREE_NOALLOC_MAX_QUERIES 65536
 int dtree_knn_noalloc(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_idx,
                       float* out_dist, const dtree_opts* opts, void* stream);
+
+/*
+ * Learned leaf proposal (no counterpart in the paper's method; it only changes
+ * which leaves are evaluated first, never the result).  A small MLP
+ * (d -> 256 -> 256 -> C, FP16 tensor-core GEMMs, FP32 master weights, Adam)
+ * maps a point to the C cells of the reference tree (its subtrees at the
+ * seed level, the subtrees the seed pass evaluates) most likely to hold the
+ * point's nearest neighbours.  With opts->proposal = 1, dtree_knn evaluates
+ * each query block's top-M proposed cells together with the greedy seed
+ * subtree before the traversal, so B(N_q) starts tight; the traversal still
+ * visits every leaf the bound does not prune, so the result is exact whatever
+ * the network predicts.
+ */
+typedef struct dtree_model dtree_model;
+
+typedef struct dtree_train_opts {
+    int32_t epochs;           /* passes over the training examples (default 20) */
+    int32_t batch;            /* examples per Adam step, <= 4096 (default 256) */
+    float lr;                 /* Adam step size (default 1e-3) */
+    int32_t example_queries;  /* queries per example: the training tree's nodes at the level
+                                 holding about this many (default 16) */
+    int32_t seed_points;      /* cells: the reference subtrees at the level whose subtrees hold
+                                 >= this many points (default 512, the search's seed level) */
+    uint32_t seed;            /* initialisation and shuffling seed (0 = default) */
+    float* loss_out;          /* optional host array: mean training loss of each epoch */
+    int32_t loss_out_len;
+    int32_t reserved[8];      /* must be zero */
+} dtree_train_opts;
+
+/*
+ * dtree_proposal_train -- train a proposal for `ref` on the method's own
+ * answers: dtree_knn(train, ref, k) gives each training query's neighbours;
+ * each node of the training tree holding about example_queries queries is one
+ * example (input: its box centre, standardised with the reference points'
+ * mean and spread; target: the distribution of its queries' neighbours over
+ * the cells; loss: softmax cross-entropy).  `train` must be a different tree
+ * from `ref`, of the same dimension.  *out is library-owned (dtree_model_free).
+ * Returns DTREE_ERR_UNSUPPORTED off sm_103 or when the reference tree has a
+ * single cell.  Waits for the result.
+ */
+int dtree_proposal_train(const dtree_t* ref, const dtree_t* train, int32_t k,
+                         const dtree_train_opts* opts, void* stream, dtree_model** out);
+void dtree_model_free(dtree_model* model);
+/* Number of cells (output classes) of a model; -1 for NULL. */
+int dtree_model_classes(const dtree_model* model);
+/*
+ * dtree_attach_proposal -- use `model` (NULL detaches) for searches against
+ * `ref` that set opts->proposal.  The model must outlive its use and have
+ * been trained for a tree of the same dimension.
+ */
+int dtree_attach_proposal(dtree_t* ref, const dtree_model* model);
+
+/*
+ * dtree_mlp_loss_grad -- one forward and backward pass of the proposal's
+ * network with the caller's parameters, for checking the kernels:
+ *   params  device FP32: W1 [256 x d], b1 [256], W2 [256 x 256], b2 [256],
+ *           W3 [C x 256], b3 [C] (row-major, W_l maps layer l-1 to layer l)
+ *   X       device FP32 [n x d] inputs (used as given, not standardised)
+ *   T       device FP32 [n x C] target distributions (rows sum to 1)
+ *   loss    host: mean over rows of -sum_c T log softmax(Z)
+ *   grads   device FP32, the gradients of `loss`, shaped like params
+ * GEMMs run in FP16 on the tensor cores with FP32 accumulation.  n <= 4096.
+ */
+int dtree_mlp_loss_grad(int32_t d, int32_t C, const float* const* params, const float* X,
+                        const float* T, int32_t n, float* loss, float* const* grads, void* stream);
 
 /* dtree_free -- release every device allocation of the handle.  NULL-safe.
  * Must not be called while work that uses the handle is still in flight. */

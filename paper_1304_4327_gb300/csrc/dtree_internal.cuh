@@ -35,6 +35,8 @@ struct dtree {
     // frontier capacity that sufficed for the last traversal against this
     // reference tree (a sizing hint only; results never depend on it)
     int64_t cap_hint = 0;
+    // learned proposal attached to this reference tree (not owned), or null
+    const dtree_model* proposal = nullptr;
 };
 
 namespace dt {
@@ -48,6 +50,13 @@ struct ScratchArena {
     unsigned char* base;
     size_t bytes;
 };
+
+// Top-M proposed cells of `n` points (row-major n x d, device), for the seed.
+int proposal_cells(const dtree_model* md, const float* pts, int64_t n, int M, int32_t* out,
+                   cudaStream_t s);
+// Box centres (n x d) of `count` consecutive nodes of a tree.
+int box_centres(const dtree_t* t, int64_t node0, int64_t count, float* out, cudaStream_t s);
+int model_level(const dtree_model* md);
 
 // dtree_knn's checks and dispatch, with its scratch from the pool (arena
 // null) or from a fixed range.

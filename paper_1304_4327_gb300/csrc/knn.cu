@@ -83,7 +83,7 @@ __device__ __forceinline__ float box_dmin_down(const float* a, const float* b) {
 }
 
 template <int DP>
-__global__ void k_seed(const ProbDev* probs, const int32_t* blk_prob, int nblocks,
+__global__ void k_seed(const ProbDev* probs, const int32_t* blk_prob, int nblocks, int slots,
                        int32_t* seed_leaf0, int32_t* seed_nleaf) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nblocks) return;
@@ -101,8 +101,33 @@ __global__ void k_seed(const ProbDev* probs, const int32_t* blk_prob, int nblock
         n = dr < dl ? r : l;
     }
     const int span = P.hr - P.Ls;
-    seed_leaf0[g] = (int32_t)(((n + 1) << span) - 1 - P.rleaf0);
-    seed_nleaf[g] = 1 << span;
+    seed_leaf0[g * slots] = (int32_t)(((n + 1) << span) - 1 - P.rleaf0);
+    seed_nleaf[g * slots] = 1 << span;
+    for (int s = 1; s < slots; ++s) {
+        seed_leaf0[g * slots + s] = 0;
+        seed_nleaf[g * slots + s] = 0;
+    }
+}
+
+// Slots 1..M of each block's seed: its proposed cells (subtrees at the seed
+// level), skipping any cell already in the seed.
+__global__ void k_seed_proposal(const ProbDev* probs, const int32_t* blk_prob, int nblocks,
+                                int slots, const int32_t* cells, int M, int32_t* seed_leaf0,
+                                int32_t* seed_nleaf) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nblocks) return;
+    const ProbDev& P = probs[blk_prob[g]];
+    const int span = P.hr - P.Ls;
+    int used = 1;
+    for (int m = 0; m < M && used < slots; ++m) {
+        const int l0 = cells[(int64_t)g * M + m] << span;
+        bool dup = false;
+        for (int s = 0; s < used; ++s) dup |= seed_leaf0[g * slots + s] == l0;
+        if (dup) continue;
+        seed_leaf0[g * slots + used] = l0;
+        seed_nleaf[g * slots + used] = 1 << span;
+        ++used;
+    }
 }
 
 constexpr int kExpandProbs = 64;
@@ -113,8 +138,8 @@ __global__ void __launch_bounds__(256) k_expand(const ProbDev* __restrict__ prob
                                                 const float* __restrict__ Bn, const int2* fin,
                                                 const int* nin, int2* fout, int* nout, int64_t cap,
                                                 int4* outp, int* noutp, int64_t capp, int* bcount,
-                                                const int32_t* sl0, const int32_t* sn, int* overflow,
-                                                unsigned long long* stats, int np) {
+                                                const int32_t* sl0, const int32_t* sn, int slots,
+                                                int* overflow, unsigned long long* stats, int np) {
     // the first kExpandProbs problems' descriptors are staged in shared memory
     extern __shared__ ProbDev sprob[];
     for (int p = threadIdx.x; p < min(np, kExpandProbs); p += blockDim.x) sprob[p] = probs[p];
@@ -167,8 +192,7 @@ __global__ void __launch_bounds__(256) k_expand(const ProbDev* __restrict__ prob
                 } else if (qbot && rbot) {
                     const int blk = block0 + (int)(qc - qblock0);
                     const int leaf = (int)(rc - rleaf0);
-                    const int s0 = sl0[blk];
-                    if (!(leaf >= s0 && leaf < s0 + sn[blk])) {  // else evaluated by the seed
+                    if (!in_seed(sl0, sn, slots, blk, leaf)) {  // else evaluated by the seed
                         // evaluation order: squared distance between the box centres
                         float o = 0.f;
 #pragma unroll
@@ -371,19 +395,19 @@ __global__ void __launch_bounds__(256) k_csr_sort(const int64_t* off, int nb, in
 template <int DP>
 int launch_expand(const ProbDev* probs, const int32_t* node_prob, const float* Bn, const int2* fin,
                   const int* nin, int2* fout, int* nout, int64_t cap, int4* outp, int* noutp,
-                  int64_t capp, int* bcount, const int32_t* sl0, const int32_t* sn, int* overflow,
-                  unsigned long long* stats, int np, int grid, cudaStream_t s) {
+                  int64_t capp, int* bcount, const int32_t* sl0, const int32_t* sn, int slots,
+                  int* overflow, unsigned long long* stats, int np, int grid, cudaStream_t s) {
     const size_t smem = (size_t)std::min(np, kExpandProbs) * sizeof(ProbDev);
     DT_LAUNCH(k_expand<DP>, grid, 256, smem, s, probs, node_prob, Bn, fin, nin, fout, nout, cap,
-              outp, noutp, capp, bcount, sl0, sn, overflow, stats, np);
+              outp, noutp, capp, bcount, sl0, sn, slots, overflow, stats, np);
     return DTREE_OK;
 }
 
 template <int DP>
-int launch_seed(const ProbDev* probs, const int32_t* blk_prob, int nblocks,
+int launch_seed(const ProbDev* probs, const int32_t* blk_prob, int nblocks, int slots,
                 int32_t* seed_leaf0, int32_t* seed_nleaf, cudaStream_t s) {
-    DT_LAUNCH(k_seed<DP>, (nblocks + 127) / 128, 128, 0, s, probs, blk_prob, nblocks, seed_leaf0,
-              seed_nleaf);
+    DT_LAUNCH(k_seed<DP>, (nblocks + 127) / 128, 128, 0, s, probs, blk_prob, nblocks, slots,
+              seed_leaf0, seed_nleaf);
     return DTREE_OK;
 }
 
@@ -513,6 +537,7 @@ struct HostProb {
     int64_t* out_idx;
     float* out_dist;
     int qb;  // queries per block, or 0 for the call's option
+    const dtree_model* prop;  // learned proposal to seed with, or null
 };
 
 // Candidate-list lengths come in buckets of 4, 8, 16, 24 and 32.
@@ -525,7 +550,7 @@ inline int kc_bucket(int need) {
 // problems' blocks, pairs and queries.
 template <int DP>
 int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int prec, int spin,
-                   cudaStream_t s, dtree_stats* st, const ScratchArena* arena) {
+                   int nprop, cudaStream_t s, dtree_stats* st, const ScratchArena* arena) {
     const int64_t launches0 = g_launches.load();
     const int fmt = prec == DTREE_PREC_BF16 ? 1 : prec == DTREE_PREC_TF32 ? 2 : 0;
     // list length: k plus room for the candidates inside the error band
@@ -560,8 +585,14 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int pre
         P.hr = tr->height;
         P.rleaf0 = ((int64_t)1 << P.hr) - 1;
         P.Ls = 0;
-        const int seed = std::max(hp[i].k + 1, seed_pts);
-        while (P.Ls < P.hr && (m >> (P.Ls + 1)) >= seed) ++P.Ls;
+        if (nprop > 0) {
+            // seed subtrees at the proposal's cell level, so that the greedy
+            // subtree and the proposed cells are equal or disjoint
+            P.Ls = std::min(model_level(hp[i].prop), P.hr);
+        } else {
+            const int seed = std::max(hp[i].k + 1, seed_pts);
+            while (P.Ls < P.hr && (m >> (P.Ls + 1)) >= seed) ++P.Ls;
+        }
         P.qpts = tq->pts;
         P.qidx = tq->idx;
         P.qbeg = tq->nbeg;
@@ -605,8 +636,9 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int pre
     DT_TRY(P.get(&node_prob, NN));
     DT_TRY(P.get(&items, NI));
     DT_TRY(P.get(&roots, np));
-    DT_TRY(P.get(&sl0, NB));
-    DT_TRY(P.get(&sn, NB));
+    const int slots = 1 + nprop;
+    DT_TRY(P.get(&sl0, (size_t)NB * slots));
+    DT_TRY(P.get(&sn, (size_t)NB * slots));
     DT_TRY(P.get(&cand_d, (size_t)KC * NQ));
     DT_TRY(P.get(&cand_i, (size_t)KC * NQ));
     DT_TRY(P.get(&qub, NQ));
@@ -634,8 +666,23 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int pre
     PhaseTimer tm(s, st != nullptr);
     tm.mark();  // 0
 
-    // 1. seed
-    DT_TRY(launch_seed<DP>(probs, blk_prob, NB, sl0, sn, s));
+    // 1. seed: the greedy subtree of each block, plus its proposed cells
+    DT_TRY(launch_seed<DP>(probs, blk_prob, NB, slots, sl0, sn, s));
+    if (nprop > 0) {
+        int32_t* cells;
+        float* centres;
+        int64_t maxnb = 0;
+        for (int i = 0; i < np; ++i) maxnb = std::max<int64_t>(maxnb, pd[i].nblocks);
+        DT_TRY(P.get(&cells, (size_t)NB * nprop));
+        DT_TRY(P.get(&centres, (size_t)maxnb * hp[0].tq->d));
+        for (int i = 0; i < np; ++i) {
+            DT_TRY(box_centres(hp[i].tq, pd[i].qblock0, pd[i].nblocks, centres, s));
+            DT_TRY(proposal_cells(hp[i].prop, centres, pd[i].nblocks, nprop,
+                                  cells + (size_t)pd[i].block0 * nprop, s));
+        }
+        DT_LAUNCH(k_seed_proposal, (NB + 127) / 128, 128, 0, s, probs, blk_prob, NB, slots, cells,
+                  nprop, sl0, sn);
+    }
     TileArgs a{};
     a.probs = probs;
     a.blk_prob = blk_prob;
@@ -644,6 +691,7 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int pre
     a.nq_all = NQ;
     a.seed_leaf0 = sl0;
     a.seed_nleaf = sn;
+    a.seed_slots = slots;
     a.cand_d = cand_d;
     a.cand_i = cand_i;
     a.qub = qub;
@@ -742,8 +790,8 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int pre
             }
             DT_CHECK(cudaMemsetAsync(nc[nx], 0, sizeof(int), s));
             DT_TRY(launch_expand<DP>(probs, node_prob, Bn, F[cur], nc[cur], F[nx], nc[nx], fcap[nx],
-                                     outp, ctr + 7, ocap, bcount, sl0, sn, ctr + 4, dstats, np,
-                                     egrid, s));
+                                     outp, ctr + 7, ocap, bcount, sl0, sn, slots, ctr + 4, dstats,
+                                     np, egrid, s));
             int hv[4];
             DT_CHECK(cudaMemcpyAsync(hv, ctr + 4, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
             DT_CHECK(cudaStreamSynchronize(s));
@@ -774,7 +822,7 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int pre
         for (int t = 0; t < steps; ++t) {
             DT_CHECK(cudaMemsetAsync(no, 0, sizeof(int), s));
             DT_TRY(launch_expand<DP>(probs, node_prob, Bn, fi, ni, fo, no, cap, outp, ctr + 7, cap,
-                                     bcount, sl0, sn, ctr + 4, dstats, np, egrid, s));
+                                     bcount, sl0, sn, slots, ctr + 4, dstats, np, egrid, s));
             std::swap(fi, fo);
             std::swap(ni, no);
         }
@@ -842,7 +890,7 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int pre
 
 // Shared option checks of dtree_knn and dtree_knn_batch.
 struct KnnOpts {
-    int prec, qb, seed_pts, spin;
+    int prec, qb, seed_pts, spin, nprop;
 };
 
 int parse_opts(const dtree_opts* o, KnnOpts* ko) {
@@ -853,7 +901,8 @@ int parse_opts(const dtree_opts* o, KnnOpts* ko) {
     if (ko->prec < DTREE_PREC_FP32 || ko->prec > DTREE_PREC_BF16) return DTREE_ERR_INVALID_ARG;
     ko->qb = (o && o->query_block) ? o->query_block : 128;
     if (ko->qb < 16 || ko->qb > 128) return DTREE_ERR_INVALID_ARG;
-    if (o && o->proposal) return DTREE_ERR_NOT_TRAINED;
+    ko->nprop = o ? o->proposal : 0;
+    if (ko->nprop < 0 || ko->nprop > 8) return DTREE_ERR_INVALID_ARG;
     ko->seed_pts = (o && o->seed_points > 0) ? o->seed_points : 512;
     ko->spin = (o && o->spin_budget > 0) ? o->spin_budget : (1 << 20);
     return DTREE_OK;
@@ -874,17 +923,24 @@ int check_problem(const dtree_t* query, const dtree_t* ref, int32_t k, const int
     hp->out_idx = const_cast<int64_t*>(out_idx);
     hp->out_dist = const_cast<float*>(out_dist);
     hp->qb = 0;
+    hp->prop = ref->proposal;
     return DTREE_OK;
 }
 
 int run_group(int dp, const HostProb* hp, int np, const KnnOpts& ko, cudaStream_t s,
               dtree_stats* st, const ScratchArena* arena) {
+    if (ko.nprop > 0) {
+        // every problem needs a proposal; the seed's model pass allocates
+        if (arena) return DTREE_ERR_UNSUPPORTED;
+        for (int i = 0; i < np; ++i)
+            if (!hp[i].prop) return DTREE_ERR_NOT_TRAINED;
+    }
     switch (dp) {
-        case 4: return knn_batch_impl<4>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, s, st, arena);
-        case 8: return knn_batch_impl<8>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, s, st, arena);
-        case 16: return knn_batch_impl<16>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, s, st, arena);
-        case 32: return knn_batch_impl<32>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, s, st, arena);
-        default: return knn_batch_impl<64>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, s, st, arena);
+        case 4: return knn_batch_impl<4>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, ko.nprop, s, st, arena);
+        case 8: return knn_batch_impl<8>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, ko.nprop, s, st, arena);
+        case 16: return knn_batch_impl<16>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, ko.nprop, s, st, arena);
+        case 32: return knn_batch_impl<32>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, ko.nprop, s, st, arena);
+        default: return knn_batch_impl<64>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, ko.nprop, s, st, arena);
     }
 }
 

@@ -73,8 +73,9 @@ struct TileArgs {
     int nitems;
     int64_t nq_all;             // rows of the per-query arrays (all problems' queries)
     // candidates
-    const int32_t* seed_leaf0;  // per block: first seed leaf
-    const int32_t* seed_nleaf;  // per block: seed leaves
+    const int32_t* seed_leaf0;  // per block and seed slot: first leaf of the slot's subtree
+    const int32_t* seed_nleaf;  // per block and seed slot: its leaves (0: an unused slot)
+    int seed_slots;             // seed slots per block (the greedy subtree, proposed cells)
     const int64_t* csr_off;     // per block: [off[b], off[b+1]) in csr_leaf / csr_dmin, in
                                 //   evaluation order (windows sorted by box-centre distance)
     const int32_t* csr_leaf;
@@ -103,17 +104,45 @@ template <int DP>
 int launch_tile_tc(const TileArgs& a, int fmt, int kc, int mode, int items, int* err, int spin,
                    cudaStream_t s);
 
+// A block's seed: up to `slots` disjoint subtrees of the reference tree,
+// slot s covering leaves [leaf0[s], leaf0[s] + nleaf[s]).
+__device__ __forceinline__ int seed_count(const int32_t* sn, int slots, int blk) {
+    int t = 0;
+    for (int s = 0; s < slots; ++s) t += sn[blk * slots + s];
+    return t;
+}
+
+// The ci-th seed leaf of a block (slots in order).
+__device__ __forceinline__ int seed_leaf(const int32_t* sl0, const int32_t* sn, int slots, int blk,
+                                         int ci) {
+    for (int s = 0; s < slots; ++s) {
+        const int n = sn[blk * slots + s];
+        if (ci < n) return sl0[blk * slots + s] + ci;
+        ci -= n;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ bool in_seed(const int32_t* sl0, const int32_t* sn, int slots, int blk,
+                                        int leaf) {
+    for (int s = 0; s < slots; ++s) {
+        const int l0 = sl0[blk * slots + s];
+        if (leaf >= l0 && leaf < l0 + sn[blk * slots + s]) return true;
+    }
+    return false;
+}
+
 // The traversal's frontier holds (global query node, reference node) pairs;
 // node_prob gives each global query node's problem.
 template <int DP>
 int launch_expand(const ProbDev* probs, const int32_t* node_prob, const float* Bn, const int2* fin,
                   const int* nin, int2* fout, int* nout, int64_t cap, int4* outp, int* nout_p,
                   int64_t cap_p, int* bcount, const int32_t* seed_leaf0,
-                  const int32_t* seed_nleaf, int* overflow, unsigned long long* stats, int np,
-                  int grid, cudaStream_t s);
+                  const int32_t* seed_nleaf, int seed_slots, int* overflow,
+                  unsigned long long* stats, int np, int grid, cudaStream_t s);
 
 template <int DP>
-int launch_seed(const ProbDev* probs, const int32_t* blk_prob, int nblocks,
+int launch_seed(const ProbDev* probs, const int32_t* blk_prob, int nblocks, int seed_slots,
                 int32_t* seed_leaf0, int32_t* seed_nleaf, cudaStream_t s);
 
 int occupancy_grid(const void* kernel, int threads, size_t smem);

@@ -240,7 +240,7 @@ enum { BAR_EPI = 1, BAR_CONV = 2, BAR_G0 = 3 };
 // shared memory, in list order (a block's list is sorted nearest-first).
 template <int NC, int MODE>
 __device__ __forceinline__ void load_window(const TileArgs& a, const ProbDev& P, int64_t w0,
-                                            int wn, int nseed, int sleaf0, int64_t c0,
+                                            int wn, int nseed, int blk, int64_t c0,
                                             uint64_t* skey, int4* srow) {
     const int lane = threadIdx.x & 31;
     for (int i = lane; i < wn; i += 32) {
@@ -248,7 +248,7 @@ __device__ __forceinline__ void load_window(const TileArgs& a, const ProbDev& P,
         int leaf;
         float dmin = 0.f;
         if (ci < nseed) {
-            leaf = sleaf0 + (int)ci;
+            leaf = seed_leaf(a.seed_leaf0, a.seed_nleaf, a.seed_slots, blk, (int)ci);
         } else {
             leaf = a.csr_leaf[c0 + ci - nseed];
             dmin = a.csr_dmin[c0 + ci - nseed];
@@ -415,8 +415,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
         if (role == 2) {
             // ================= planner (warp 8) =================
             const float Bq = a.Bn ? a.Bn[P.node0 + qnode] : INFINITY;
-            const int nseed = MODE == MODE_MAIN ? 0 : a.seed_nleaf[blk];
-            const int sleaf0 = MODE == MODE_MAIN ? 0 : a.seed_leaf0[blk];
+            const int nseed = MODE == MODE_MAIN ? 0 : seed_count(a.seed_nleaf, a.seed_slots, blk);
             const int64_t c0 = MODE == MODE_SEED ? 0 : a.csr_off[blk];
             const int64_t c1 = MODE == MODE_SEED ? 0 : a.csr_off[blk + 1];
             const int64_t ntot = nseed + (c1 - c0);
@@ -424,7 +423,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
             for (int64_t w0 = 0; w0 < ntot && !fail; w0 += S::SORTCAP) {
                 const int wn = (int)(ntot - w0 < S::SORTCAP ? ntot - w0 : S::SORTCAP);
                 long long t0 = clock64();
-                load_window<S::SORTCAP, MODE>(a, P, w0, wn, nseed, sleaf0, c0, skey, srow);
+                load_window<S::SORTCAP, MODE>(a, P, w0, wn, nseed, blk, c0, skey, srow);
                 if (x.timers && lane == 0)
                     atomicAdd(&x.timers[TT_PLAN_WINDOW], (unsigned long long)(clock64() - t0));
                 int cur = 0, part = 0;

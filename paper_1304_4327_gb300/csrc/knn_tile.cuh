@@ -107,7 +107,7 @@ __device__ __forceinline__ float ub_of(T kth) {
 // (first row, rows, stage offset) entry per run of rows.
 template <int TN, int MODE>
 __device__ __forceinline__ void stage_fill(const TileArgs& a, const ProbDev& P, int64_t w0,
-                                           int wn, int nseed, int sleaf0, int64_t c0, int3* stab,
+                                           int wn, int nseed, int blk, int64_t c0, int3* stab,
                                            unsigned long long& n_skip, unsigned long long& n_eval,
                                            int& s_cur, int& s_part, int& s_nst, int& s_ntab,
                                            const float Bc) {
@@ -126,7 +126,7 @@ __device__ __forceinline__ void stage_fill(const TileArgs& a, const ProbDev& P, 
             } else {
                 int64_t ci = w0 + c;
                 if (ci < nseed) {
-                    leaf = sleaf0 + (int)ci;
+                    leaf = seed_leaf(a.seed_leaf0, a.seed_nleaf, a.seed_slots, blk, (int)ci);
                 } else {
                     leaf = a.csr_leaf[c0 + ci - nseed];
                     dmin = a.csr_dmin[c0 + ci - nseed];
@@ -274,8 +274,7 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
             };
             refresh_bound();
 
-            const int nseed = MODE == MODE_MAIN ? 0 : a.seed_nleaf[blk];
-            const int sleaf0 = MODE == MODE_MAIN ? 0 : a.seed_leaf0[blk];
+            const int nseed = MODE == MODE_MAIN ? 0 : seed_count(a.seed_nleaf, a.seed_slots, blk);
             const int64_t c0 = MODE == MODE_SEED ? 0 : a.csr_off[blk];
             const int64_t c1 = MODE == MODE_SEED ? 0 : a.csr_off[blk + 1];
             const int64_t ntot = nseed + (c1 - c0);
@@ -291,7 +290,7 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
                 while (s_cur < wn) {
                     // ---- warp 0 fills the stage with whole or partial leaves
                     if (warp == 0)
-                        stage_fill<TN, MODE>(a, P, w0, wn, nseed, sleaf0, c0, stab, n_skip,
+                        stage_fill<TN, MODE>(a, P, w0, wn, nseed, blk, c0, stab, n_skip,
                                              n_eval, s_cur, s_part, s_nst, s_ntab, s_B);
                     __syncthreads();
                     // ---- all warps copy the staged rows
@@ -494,7 +493,7 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
         ld[j] = (T)INFINITY;
         li[j] = kEmptyIdx;
     }
-    const int nseed = a.seed_nleaf[blk], sleaf0 = a.seed_leaf0[blk];
+    const int nseed = seed_count(a.seed_nleaf, a.seed_slots, blk);
     const int64_t c0 = a.csr_off[blk], c1 = a.csr_off[blk + 1];
     const int64_t ntot = nseed + (c1 - c0);
     if (tid == 0) s_n = 0;
@@ -505,7 +504,7 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
         int leaf = -1;
         if (c < ntot) {
             if (c < nseed) {
-                leaf = sleaf0 + (int)c;
+                leaf = seed_leaf(a.seed_leaf0, a.seed_nleaf, a.seed_slots, blk, (int)c);
             } else if (!(a.csr_dmin[c0 + c - nseed] > ub)) {
                 leaf = a.csr_leaf[c0 + c - nseed];
             }

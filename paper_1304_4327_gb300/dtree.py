@@ -43,6 +43,13 @@ class dtree_problem(ctypes.Structure):
                 ("out_idx", _P), ("out_dist", _P)]
 
 
+class dtree_train_opts(ctypes.Structure):
+    _fields_ = [("epochs", _I32), ("batch", _I32), ("lr", ctypes.c_float),
+                ("example_queries", _I32), ("seed_points", _I32), ("seed", ctypes.c_uint32),
+                ("loss_out", ctypes.POINTER(ctypes.c_float)), ("loss_out_len", _I32),
+                ("reserved", _I32 * 8)]
+
+
 class DTreeError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -82,6 +89,18 @@ def _load() -> ctypes.CDLL:
     lib.dtree_knn_noalloc.argtypes = [_P, _P, _I32, _P, _P, ctypes.POINTER(dtree_opts), _P]
     lib.dtree_knn_batch.argtypes = [_I32, ctypes.POINTER(dtree_problem), ctypes.POINTER(dtree_opts),
                                     _P, ctypes.POINTER(dtree_stats)]
+    lib.dtree_proposal_train.argtypes = [_P, _P, _I32, ctypes.POINTER(dtree_train_opts), _P,
+                                         ctypes.POINTER(_P)]
+    lib.dtree_proposal_train.restype = ctypes.c_int
+    lib.dtree_model_free.argtypes = [_P]
+    lib.dtree_model_free.restype = None
+    lib.dtree_model_classes.argtypes = [_P]
+    lib.dtree_model_classes.restype = ctypes.c_int
+    lib.dtree_attach_proposal.argtypes = [_P, _P]
+    lib.dtree_attach_proposal.restype = ctypes.c_int
+    lib.dtree_mlp_loss_grad.argtypes = [_I32, _I32, ctypes.POINTER(_P), _P, _P, _I32,
+                                        ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_P), _P]
+    lib.dtree_mlp_loss_grad.restype = ctypes.c_int
     for f in (lib.dtree_build, lib.dtree_knn, lib.dtree_export, lib.dtree_knn_noalloc,
               lib.dtree_knn_batch):
         f.restype = ctypes.c_int
@@ -175,7 +194,8 @@ def dtree_build(points: torch.Tensor, leaf_size: int = 32, stream=None) -> Tree:
 
 def dtree_knn(query: Optional[Tree], ref: Tree, k: int, precision: str = "fp32",
               query_block: int = 0, seed_points: int = 0, out_idx: Optional[torch.Tensor] = None,
-              out_dist: Optional[torch.Tensor] = None, stream=None, with_stats: bool = False):
+              out_dist: Optional[torch.Tensor] = None, stream=None, with_stats: bool = False,
+              proposal: int = 0):
     """Exact kNN of every point of ``query`` (None = monochromatic) in ``ref``.
 
     Returns (idx int64 (n_q, k), dist float32 (n_q, k)) on the device, plus a
@@ -195,7 +215,8 @@ def dtree_knn(query: Optional[Tree], ref: Tree, k: int, precision: str = "fp32",
         raise ValueError("out_idx must be a contiguous int64 (n_q, k) tensor")
     if out_dist.shape != (nq, k) or out_dist.dtype != torch.float32 or not out_dist.is_contiguous():
         raise ValueError("out_dist must be a contiguous float32 (n_q, k) tensor")
-    o = _opts(precision=PRECISIONS[precision], query_block=query_block, seed_points=seed_points)
+    o = _opts(precision=PRECISIONS[precision], query_block=query_block, seed_points=seed_points,
+              proposal=proposal)
     st = dtree_stats()
     rc = _lib.dtree_knn(None if query is None else query.handle, ref.handle, int(k),
                         ctypes.c_void_p(out_idx.data_ptr()), ctypes.c_void_p(out_dist.data_ptr()),
@@ -208,7 +229,8 @@ def dtree_knn(query: Optional[Tree], ref: Tree, k: int, precision: str = "fp32",
 
 
 def dtree_knn_batch(problems, precision: str = "fp32", query_block: int = 0,
-                    seed_points: int = 0, stream=None, with_stats: bool = False):
+                    seed_points: int = 0, stream=None, with_stats: bool = False,
+                    proposal: int = 0):
     """Many independent kNN problems in one call.
 
     ``problems``: a sequence of (query Tree or None, ref Tree, k) or
@@ -234,7 +256,8 @@ def dtree_knn_batch(problems, precision: str = "fp32", query_block: int = 0,
         arr[i].query_block = qb
         arr[i].out_idx = oi.data_ptr() if oi.numel() else None
         arr[i].out_dist = od.data_ptr() if od.numel() else None
-    o = _opts(precision=PRECISIONS[precision], query_block=query_block, seed_points=seed_points)
+    o = _opts(precision=PRECISIONS[precision], query_block=query_block, seed_points=seed_points,
+              proposal=proposal)
     st = dtree_stats()
     rc = _lib.dtree_knn_batch(n, arr, ctypes.byref(o), _stream(stream),
                               ctypes.byref(st) if with_stats else None)
@@ -243,6 +266,72 @@ def dtree_knn_batch(problems, precision: str = "fp32", query_block: int = 0,
     if with_stats:
         return outs, {f: int(getattr(st, f)) for f in STAT_FIELDS}
     return outs
+
+
+class Model:
+    """A trained leaf proposal (library-owned; freed by free() or on collection)."""
+
+    def __init__(self, handle: int, losses):
+        self.handle = handle
+        self.losses = losses
+
+    @property
+    def classes(self) -> int:
+        return int(_lib.dtree_model_classes(self.handle))
+
+    def free(self) -> None:
+        if self.handle:
+            _lib.dtree_model_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def dtree_proposal_train(ref: Tree, train: Tree, k: int, epochs: int = 0, batch: int = 0,
+                         lr: float = 0.0, example_queries: int = 0, seed_points: int = 0,
+                         seed: int = 0, stream=None) -> Model:
+    """Train a leaf proposal for ``ref`` on the method's own kNN answers for the
+    points of ``train`` (see dtree.h); returns the model and its per-epoch losses."""
+    n_ep = epochs if epochs > 0 else 20
+    losses = (ctypes.c_float * n_ep)()
+    o = dtree_train_opts(epochs=epochs, batch=batch, lr=lr, example_queries=example_queries,
+                         seed_points=seed_points, seed=seed, loss_out=losses, loss_out_len=n_ep)
+    h = _P()
+    rc = _lib.dtree_proposal_train(ref.handle, train.handle, int(k), ctypes.byref(o),
+                                   _stream(stream), ctypes.byref(h))
+    if rc != DTREE_OK:
+        raise DTreeError(rc, "dtree_proposal_train")
+    return Model(h.value, [float(x) for x in losses])
+
+
+def dtree_attach_proposal(ref: Tree, model: Optional[Model]) -> None:
+    rc = _lib.dtree_attach_proposal(ref.handle, None if model is None else model.handle)
+    if rc != DTREE_OK:
+        raise DTreeError(rc, "dtree_attach_proposal")
+    ref._proposal = model  # keep the model alive while attached
+
+
+def dtree_mlp_loss_grad(params, X: torch.Tensor, T: torch.Tensor, stream=None):
+    """Loss and gradients of the proposal network (W1, b1, W2, b2, W3, b3 as
+    float32 CUDA tensors) on inputs X (n x d) against targets T (n x C)."""
+    params = [p.contiguous() for p in params]
+    n, d = X.shape
+    C = T.shape[1]
+    grads = [torch.empty_like(p) for p in params]
+    pp = (_P * 6)(*[p.data_ptr() for p in params])
+    gp = (_P * 6)(*[g.data_ptr() for g in grads])
+    loss = ctypes.c_float()
+    rc = _lib.dtree_mlp_loss_grad(int(d), int(C), pp, X.contiguous().data_ptr(),
+                                  T.contiguous().data_ptr(), int(n), ctypes.byref(loss), gp,
+                                  _stream(stream))
+    if rc != DTREE_OK:
+        raise DTreeError(rc, "dtree_mlp_loss_grad")
+    torch.cuda.current_stream().synchronize()
+    return float(loss.value), grads
 
 
 NOALLOC_MAX_QUERIES = 65536
