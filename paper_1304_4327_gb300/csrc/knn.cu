@@ -540,9 +540,10 @@ struct HostProb {
     const dtree_model* prop;  // learned proposal to seed with, or null
 };
 
-// Candidate-list lengths come in buckets of 4, 8, 16, 24 and 32.
+// Candidate-list lengths come in buckets of 4, 8, 16, 24, 32, 48 and 64.
 inline int kc_bucket(int need) {
-    return need <= 4 ? 4 : need <= 8 ? 8 : need <= 16 ? 16 : need <= 24 ? 24 : 32;
+    return need <= 4 ? 4 : need <= 8 ? 8 : need <= 16 ? 16 : need <= 24 ? 24 : need <= 32 ? 32
+           : need <= 48 ? 48 : 64;
 }
 
 // The search for a batch of problems whose points share the padded dimension
@@ -558,9 +559,11 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int pre
     // beyond 32 dimensions); buckets 4, 8, 16, 24, 32
     int kmax = 0;
     for (int i = 0; i < np; ++i) kmax = std::max(kmax, hp[i].k);
-    if (kmax + 1 > 32) return DTREE_ERR_UNSUPPORTED;
     const int kc_need = fmt == 1 ? (DP <= 32 ? kmax + 14 : 2 * kmax + 12) : fmt == 2 ? kmax + 14 : kmax + 1;
-    const int KC = kc_bucket(kc_need);
+    // float32 lists hold up to 64 entries (k <= 63), tensor-core lists up to 32
+    // (k <= 31; a band wider than the list sends its queries to the fallback)
+    if (kmax + 1 > (fmt ? 32 : 64)) return DTREE_ERR_UNSUPPORTED;
+    const int KC = std::min(kc_bucket(kc_need), fmt ? 32 : 64);
 
     // the problems' layout in the batch-wide arrays
     ProbDev one[1];

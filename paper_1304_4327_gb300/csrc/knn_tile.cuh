@@ -643,6 +643,8 @@ int launch_query_fb(const TileArgs& a, int kc, int nfbq, bool exact, cudaStream_
         DT_FB_CASE(16)
         DT_FB_CASE(24)
         DT_FB_CASE(32)
+        DT_FB_CASE(48)
+        DT_FB_CASE(64)
         default:
             return DTREE_ERR_UNSUPPORTED;
     }
@@ -673,6 +675,8 @@ int launch_tile_cc(const TileArgs& a, int kc, int mode, int items, cudaStream_t 
         DT_TILE_CASE(16)
         DT_TILE_CASE(24)
         DT_TILE_CASE(32)
+        DT_TILE_CASE(48)
+        DT_TILE_CASE(64)
         default:
             return DTREE_ERR_UNSUPPORTED;
     }

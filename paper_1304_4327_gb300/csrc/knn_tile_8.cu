@@ -3,5 +3,4 @@
 
 namespace dt {
 template int launch_tile_cc<8>(const TileArgs&, int, int, int, cudaStream_t);
-template int launch_query_fb<8>(const TileArgs&, int, int, bool, cudaStream_t);
 }  // namespace dt

@@ -241,6 +241,30 @@ def test_powerlaw64_scaled(dt):
     check(dt, W.ref, W.query, 31, W.leaf_size)
 
 
+def test_powerlaw64_k50_scaled(dt):
+    # the power-law workload's own k (lists of 64 on the CUDA cores)
+    W = inputs.powerlaw64(n_ref=40_000, n_query=3_000)
+    assert W.k == 50
+    check(dt, W.ref, W.query, W.k, W.leaf_size)
+    check(dt, W.ref[:20_000], None, W.k, W.leaf_size)
+    # tensor-core lists hold at most 32 entries
+    for prec in ("bf16", "tf32"):
+        with pytest.raises(dt.DTreeError) as e:
+            run(dt, W.ref, W.query, W.k, W.leaf_size, precision=prec)
+        assert e.value.status == -7
+
+
+@pytest.mark.parametrize("k", [32, 47, 48, 63])
+def test_large_k(dt, k):
+    R = inputs.gaussian(6000, 5, 200 + k)
+    Q = inputs.uniform(900, 5, 300 + k)
+    check(dt, R, Q, k, leaf=16)
+    check(dt, R, None, k, leaf=16)
+    with pytest.raises(dt.DTreeError) as e:
+        run(dt, R, Q, 64, 16)
+    assert e.value.status == -7
+
+
 def test_batched_problems_scaled(dt):
     for spec in inputs.batched_specs()[:24]:
         W = inputs.batched_problem(spec, n_cap=20_000)
