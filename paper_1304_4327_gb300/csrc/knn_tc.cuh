@@ -77,11 +77,17 @@ struct TcShape {
     static constexpr int RB = KP * TcFmt<FMT>::esize;  // bytes per operand row
     static constexpr int NCH = RB / 16;                // 16-byte chunks per row
     static constexpr int SBO = NCH * 128;
-    static constexpr int TN = 128;                     // reference points per tile
-    static constexpr int NS = RB >= 160 ? 2 : 4;       // operand slots = TMEM accumulators
+    // reference points per tile: 256 (the MMA's widest N) where the operand
+    // slots fit shared memory, so per-tile hand-overs are paid per 256 points
+    static constexpr int TN = DP <= 16 ? 256 : 128;
+    // TMEM accumulators: one per epilogue group (2 x TN <= 512 columns)
+    static constexpr int NS = 2;
+    // operand slots in shared memory: the converters fill ahead of the groups
+    // (each group issues its own MMAs from them)
+    static constexpr int NB = RB >= 160 ? 2 : (TN == 256 ? 3 : 4);
     static constexpr int NK = KP / TcFmt<FMT>::kstep;  // MMAs per tile
-    static constexpr int SORTCAP = DP >= 64 ? 512 : 1024;        // candidates per window
-    static constexpr int CB = DP >= 32 ? 8 : 16;                 // deferred insertions per thread
+    static constexpr int SORTCAP = (DP >= 64 || TN == 256) ? 512 : 1024;  // candidates per window
+    static constexpr int CB = (DP >= 32 || TN == 256) ? 8 : 16;           // deferred insertions per thread
     static constexpr int RAWB = TN * DP * 4;                     // raw float32 rows of a stage
     static constexpr int RINGB = (DP >= 32 || RB >= 128) ? 32768 : 65536;  // raw ring budget
     static constexpr int NR = RINGB / RAWB > 8 ? 8 : (RINGB / RAWB < 2 ? 2 : RINGB / RAWB);
@@ -94,10 +100,10 @@ struct TcSmem {
     static constexpr int MERGE = kQB * KC * 8;                       // lists / re-rank at block end
     static constexpr int RING = S::NR * S::RAWB;
     static constexpr int OFF_A = 0;                                  // 128 x RB
-    static constexpr int OFF_B = OFF_A + kQB * S::RB;                // NS x TN x RB
-    static constexpr int OFF_RAW = OFF_B + S::NS * S::TN * S::RB;    // NR x TN x DP float (or merge)
-    static constexpr int OFF_POS = OFF_RAW + (RING > MERGE ? RING : MERGE);  // NS x TN int
-    static constexpr int OFF_RPOS = OFF_POS + S::NS * S::TN * 4;     // NR x TN int
+    static constexpr int OFF_B = OFF_A + kQB * S::RB;                // NB x TN x RB
+    static constexpr int OFF_RAW = OFF_B + S::NB * S::TN * S::RB;    // NR x TN x DP float (or merge)
+    static constexpr int OFF_POS = OFF_RAW + (RING > MERGE ? RING : MERGE);  // (NB + NS) x TN int
+    static constexpr int OFF_RPOS = OFF_POS + (S::NB + S::NS) * S::TN * 4;  // NR x TN int
     static constexpr int OFF_KEY = OFF_RPOS + S::NR * S::TN * 4;     // SORTCAP uint64
     static constexpr int OFF_ROW = OFF_KEY + S::SORTCAP * 8;         // SORTCAP int4
     static constexpr int OFF_SCR = OFF_ROW + S::SORTCAP * 16;        // 2 x 32 x 128 float
@@ -234,7 +240,7 @@ enum TcTimer {
 static_assert(TT_N <= 32, "the diagnostic timer buffer holds 32 counters");
 
 // Named barriers of the pipelined kernel (0 is __syncthreads).
-enum { BAR_EPI = 1, BAR_CONV = 2, BAR_G0 = 3 };
+enum { BAR_EPI = 1, BAR_CONV = 2, BAR_G0 = 3, BAR_G1 = 4 };
 
 // The planner warp: read the window's candidates (row range and d_min) into
 // shared memory, in list order (a block's list is sorted nearest-first).
@@ -280,7 +286,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
     using S = TcShape<FMT, DP>;
     using L = TcSmem<FMT, DP, KC>;
     using Bd = TcBound<FMT, DP>;
-    constexpr int TN = S::TN, NS = S::NS, NR = S::NR;
+    constexpr int TN = S::TN, NS = S::NS, NB = S::NB, NR = S::NR;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem + L::OFF_A;
     unsigned char* sB = smem + L::OFF_B;
@@ -292,12 +298,13 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
     float* sscr = reinterpret_cast<float*>(smem + L::OFF_SCR);
     float* sbuf = reinterpret_cast<float*>(smem + L::OFF_BUF);
     float* scen = reinterpret_cast<float*>(smem + L::OFF_CEN);
-    __shared__ uint64_t full[NS], empty[NS], raw_full[NR], raw_empty[NR];
-    __shared__ int smeta[NS], srmeta[NR];
+    __shared__ uint64_t acc_full[NS], raw_full[NR], raw_empty[NR], op_full[NB], op_empty[NB];
+    __shared__ int ometa[NB], srmeta[NR];
+    __shared__ volatile int s_gfail[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_item;
     __shared__ ProbDev s_prob;
-    __shared__ volatile int s_fail, s_cmeta;
+    __shared__ volatile int s_fail, s_cmeta, s_cok;
     __shared__ volatile float s_wmax[8], s_wmin[8];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -307,14 +314,17 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
     unsigned long long n_skip = 0, n_eval = 0, n_pp = 0, n_re = 0, n_ins = 0;
 
     if (tid == 0) {
-        for (int i = 0; i < NS; ++i) {
-            tc::mbar_init(&full[i], 2);   // tcgen05.commit + the converters' release
-            tc::mbar_init(&empty[i], 4);  // the four warps of the consuming group
-        }
+        for (int i = 0; i < NS; ++i) tc::mbar_init(&acc_full[i], 1);  // tcgen05.commit
         for (int i = 0; i < NR; ++i) {
             tc::mbar_init(&raw_full[i], 1);   // the planner's arrival (+ copied bytes)
             tc::mbar_init(&raw_empty[i], 1);  // the converters' release
         }
+        for (int i = 0; i < NB; ++i) {
+            tc::mbar_init(&op_full[i], 1);   // the converters' release
+            tc::mbar_init(&op_empty[i], 2);  // tcgen05.commit + the consuming group's release
+        }
+        s_gfail[0] = 0;
+        s_gfail[1] = 0;
         tc::fence_mbar_init();
         s_fail = 0;
     }
@@ -325,9 +335,11 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
     const uint32_t tmem = s_tmem;
     const uint32_t idesc = tc::idesc(TcFmt<FMT>::hw, kQB, TN);
     uint32_t rtile = 0;     // planner / converters: next raw stage
-    uint32_t ptile = 0;     // converters: next operand slot use
+    uint32_t otile = 0;     // converters: next operand slot use (the barriers' phases
+                            // carry over from item to item, so the counters do too)
     uint32_t ctile = role;  // epilogue group: next operand slot use of this group
-    int last_slot = -1;
+    uint32_t acnt = 0;      // epilogue group: MMAs issued into its accumulator
+    bool pend = false;      // epilogue group leader: an MMA whose completion was not seen
 
     const ProbDev& P = s_prob;
     for (;;) {
@@ -547,11 +559,12 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
         } else if (role == 3) {
             // ================= converters (warps 9-11) =================
             const int ctid = tid - 288;
+            int32_t* opos_all = spos;  // NB x TN: the operand slots' column positions
             for (;;) {
                 const int r = rtile % NR;
                 const uint32_t ruse = rtile / NR;
-                const int slot = ptile % NS;
-                const uint32_t suse = ptile / NS;
+                const int op = otile % NB;
+                const uint32_t ouse = otile / NB;
                 long long tc0 = clock64();
                 if (ctid == 0) {
                     int m = -2;
@@ -559,7 +572,9 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                         long long tc1 = clock64();
                         if (x.timers) atomicAdd(&x.timers[TT_CONV_WAIT_RAW], (unsigned long long)(tc1 - tc0));
                         m = srmeta[r];
-                        if (m >= 0 && !tc::mbar_wait(&empty[slot], (suse & 1u) ^ 1u, x.spin_budget))
+                        // the operand slot is free once its MMA has read it and its
+                        // group has copied its column positions
+                        if (m >= 0 && !tc::mbar_wait(&op_empty[op], (ouse & 1u) ^ 1u, x.spin_budget))
                             m = -2;
                         if (x.timers) atomicAdd(&x.timers[TT_CONV_WAIT_SLOT], (unsigned long long)(clock64() - tc1));
                     }
@@ -573,21 +588,20 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                 }
                 if (m == -1) {
                     // release the stage, then one end marker for each epilogue group
+                    // (tiles alternate between the groups)
                     if (ctid == 0) {
                         tc::mbar_arrive(&raw_empty[r], 1);
                         for (int e = 0; e < 2; ++e) {
-                            const int sl = (ptile + e) % NS;
-                            const uint32_t su = (ptile + e) / NS;
-                            if (!tc::mbar_wait(&empty[sl], (su & 1u) ^ 1u, x.spin_budget)) {
-                                s_fail = 1;
-                                break;
-                            }
-                            smeta[sl] = -1;
-                            tc::mbar_arrive(&full[sl], 2);
+                            const int sl = (otile + e) % NB;
+                            const uint32_t su = (otile + e) / NB;
+                            // (on a timeout the groups' own bounded waits end them)
+                            if (!tc::mbar_wait(&op_empty[sl], (su & 1u) ^ 1u, x.spin_budget)) s_fail = 1;
+                            ometa[sl] = -1;
+                            tc::mbar_arrive(&op_full[sl], 1);
                         }
                     }
                     ++rtile;
-                    ptile += 2;
+                    otile += 2;
                     break;
                 }
                 // every converter thread observes the stage's completion itself
@@ -597,8 +611,8 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                 // centre and round the stage's rows into the operand slot
                 const float* raw = sraw + r * TN * DP;
                 const int32_t* rpos = srpos + r * TN;
-                unsigned char* sBs = sB + slot * TN * S::RB;
-                int32_t* sposs = spos + slot * TN;
+                unsigned char* sBs = sB + op * TN * S::RB;
+                int32_t* opos = opos_all + op * TN;
                 for (int row = ctid; row < TN; row += 96) {
                     if (row < m) {
                         const float4* r4 = reinterpret_cast<const float4*>(raw + row * DP);
@@ -618,7 +632,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                         for (int c = 0; c < S::NCH; ++c)
                             *reinterpret_cast<uint4*>(sBs + tc::core_offset(row, c, S::SBO)) =
                                 tc_row_chunk<FMT, DP, false>(c, xh, xl, nhi, nlo);
-                        sposs[row] = rpos[row];
+                        opos[row] = rpos[row];
                     } else {
                         // an empty column: w = +inf never qualifies
 #pragma unroll
@@ -638,54 +652,87 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                             }
                             *reinterpret_cast<uint4*>(sBs + tc::core_offset(row, c, S::SBO)) = w;
                         }
-                        sposs[row] = kEmptyIdx;
+                        opos[row] = kEmptyIdx;
                     }
                 }
                 tc::fence_proxy_async_smem();
                 tc::named_sync(BAR_CONV, 96);
                 if (ctid == 0) {
                     tc::mbar_arrive(&raw_empty[r], 1);
-                    smeta[slot] = m;
+                    ometa[op] = m;
                     n_pp += (unsigned long long)m * nq;
-                    tc::fence_after_sync();
-                    const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sBs);
-#pragma unroll
-                    for (int kk = 0; kk < S::NK; ++kk)
-                        tc::mma<TcFmt<FMT>::hw>(tmem + (uint32_t)(slot * TN),
-                                     tc::sdesc(a0 + 256u * kk, 128u, S::SBO),
-                                     tc::sdesc(b0 + 256u * kk, 128u, S::SBO), idesc, kk > 0 ? 1u : 0u);
-                    tc::mma_commit(&full[slot]);
-                    tc::mbar_arrive(&full[slot], 1);
+                    tc::mbar_arrive(&op_full[op], 1);
                     if (x.timers) {
                         atomicAdd(&x.timers[TT_CONV_WORK], (unsigned long long)(clock64() - tc2));
                         atomicAdd(&x.timers[TT_TILES], 1ull);
                     }
                 }
-                last_slot = slot;
                 ++rtile;
-                ++ptile;
+                ++otile;
             }
         } else {
             // ================= epilogue group `role` =================
             const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+            const int slot = role;  // this group's accumulator
+            const int gbar = role == 0 ? BAR_G0 : BAR_G1;
+            int32_t* sposs = spos + (NB + slot) * TN;  // its column positions
             for (;;) {
-                const int slot = ctile % NS;
-                const uint32_t use = ctile / NS;
+                // this group's next tile: operand slot op (or an end marker)
+                const int op = ctile % NB;
+                const uint32_t ouse = ctile / NB;
                 long long te0 = clock64();
-                bool ok = tc::mbar_wait(&full[slot], use & 1u, x.spin_budget);
-                ok = __all_sync(0xffffffffu, ok);
-                if (!ok) {
-                    if (lane == 0) s_fail = 1;
+                bool ok = tc::mbar_wait(&op_full[op], ouse & 1u, x.spin_budget);
+                if (!__all_sync(0xffffffffu, ok) && lane == 0) s_gfail[role] = 1;
+                const int nst = ok ? ometa[op] : -1;
+                // every warp of the group is done with the last tile (its TMEM
+                // reads and its column positions) before either is replaced
+                tc::fence_before_sync();
+                tc::named_sync(gbar, 128);
+                tc::fence_after_sync();
+                if (s_gfail[role]) {
+                    s_fail = 1;
                     break;
+                }
+                if (qt == 0) {
+                    if (nst >= 0) {
+                        const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB + op * TN * S::RB);
+#pragma unroll
+                        for (int kk = 0; kk < S::NK; ++kk)
+                            tc::mma<TcFmt<FMT>::hw>(tmem + (uint32_t)(slot * TN),
+                                                    tc::sdesc(a0 + 256u * kk, 128u, S::SBO),
+                                                    tc::sdesc(b0 + 256u * kk, 128u, S::SBO), idesc,
+                                                    kk > 0 ? 1u : 0u);
+                        tc::mma_commit(&acc_full[slot]);
+                        tc::mma_commit(&op_empty[op]);
+                        pend = true;
+                    } else {
+                        tc::mbar_arrive(&op_empty[op], 2);  // an end marker: nothing reads the slot
+                    }
+                }
+                ctile += 2;
+                if (nst < 0) break;
+                // the operand's column positions move to the accumulator's, so the
+                // operand slot can be refilled while this group works
+                for (int i = qt; i < TN; i += kQB) sposs[i] = spos[op * TN + i];
+                // the accumulator of this tile
+                ok = tc::mbar_wait(&acc_full[slot], acnt & 1u, x.spin_budget);
+                ++acnt;
+                if (!__all_sync(0xffffffffu, ok) && lane == 0) s_gfail[role] = 1;
+                tc::named_sync(gbar, 128);  // also: every position is copied
+                if (s_gfail[role]) {
+                    s_fail = 1;
+                    break;
+                }
+                if (qt == 0) {
+                    pend = false;
+                    tc::mbar_arrive(&op_empty[op], 1);  // the slot's positions are copied
                 }
                 long long te1 = clock64();
                 if (x.timers && (warp & 3) == 0 && lane == 0)
                     atomicAdd(&x.timers[TT_EPI_WAIT], (unsigned long long)(te1 - te0));
                 tc::fence_after_sync();
-                const int nst = smeta[slot];
                 bool changed = false;
-                if (nst >= 0) {
-                    const int32_t* sposs = spos + slot * TN;
+                {
                     float* scr = sscr + role * 32 * kQB + qt;
                     // insertion threshold in w units: below the list's last key and
                     // inside the error band of the current k-th key (a key above
@@ -777,13 +824,8 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                     if (x.timers && (warp & 3) == 0 && lane == 0)
                         atomicAdd(&x.timers[TT_EPI_FLUSH], (unsigned long long)(clock64() - tf1));
                 }
-                tc::fence_before_sync();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&empty[slot], 1);
                 if (x.timers && (warp & 3) == 0 && lane == 0)
                     atomicAdd(&x.timers[TT_EPI_WORK], (unsigned long long)(clock64() - te1));
-                ctile += 2;
-                if (nst < 0) break;
                 if (!__any_sync(0xffffffffu, changed)) continue;  // the published bound stands
                 long long tb0 = clock64();
                 float ub = Bd::ub(list_at(ld, kq - 1), qa);
@@ -879,11 +921,11 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
         }
         __syncthreads();
     }
-    // a failed wait may leave the last MMA in flight: wait for it (bounded)
-    // before the accumulators are released
-    if (s_fail && tid == 288 && last_slot >= 0) {
+    // a failed wait may leave an MMA in flight: its group's leader waits for it
+    // (bounded) before the accumulators are released
+    if (s_fail && pend) {
         atomicExch(x.err, 1);
-        tc::mbar_wait(&full[last_slot], ((ptile - 1) / NS) & 1u, x.spin_budget);
+        tc::mbar_wait(&acc_full[role], (acnt - 1) & 1u, x.spin_budget);
     }
     if (s_fail && tid == 0) atomicExch(x.err, 1);
     tc::fence_before_sync();
