@@ -69,13 +69,17 @@ typedef struct dtree_opts {
     int32_t query_block;   /* dtree_knn: max queries per work unit (query-tree node), 16..128
                               (default 128) */
     int32_t seed_points;   /* dtree_knn: min reference points of the seed subtree evaluated
-                              before the traversal (default 512) */
+                              before the traversal (default 64) */
     int32_t proposal;      /* dtree_knn: M > 0 evaluates each query block's top-M cells of the
                               proposal attached to the reference tree (see
                               dtree_attach_proposal) in the seed pass, M <= 8; 0: none */
     int32_t spin_budget;   /* dtree_knn: polls of a device-side wait before it gives up
                               with DTREE_ERR_TIMEOUT (default 1 << 20, about a second) */
-    int32_t reserved[10];  /* must be zero */
+    int32_t cap_leaves;    /* dtree_knn: reference leaves each query's best-first cap search
+                              may evaluate before the traversal, 1..17 (default 8); -1
+                              skips the cap pass.  The cap only tightens bounds: results
+                              are the same whatever its value */
+    int32_t reserved[9];   /* must be zero */
 } dtree_opts;
 
 /* Counters of one dtree_knn call (all zero if not requested). */

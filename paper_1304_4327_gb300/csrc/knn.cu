@@ -550,7 +550,7 @@ inline int kc_bucket(int need) {
 // DP: every phase is one launch (or one per traversal level) over all the
 // problems' blocks, pairs and queries.
 template <int DP>
-int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int prec, int spin,
+int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int cap_leaves, int prec, int spin,
                    int nprop, cudaStream_t s, dtree_stats* st, const ScratchArena* arena) {
     const int64_t launches0 = g_launches.load();
     const int fmt = prec == DTREE_PREC_BF16 ? 1 : prec == DTREE_PREC_TF32 ? 2 : 0;
@@ -645,6 +645,8 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int pre
     DT_TRY(P.get(&cand_d, (size_t)KC * NQ));
     DT_TRY(P.get(&cand_i, (size_t)KC * NQ));
     DT_TRY(P.get(&qub, NQ));
+    float* qcap = nullptr;
+    if (cap_leaves > 0) DT_TRY(P.get(&qcap, NQ));
     DT_TRY(P.get(&derr, 1));
     DT_TRY(P.get(&B1n, NN));
     DT_TRY(P.get(&An, NN));
@@ -712,6 +714,10 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int pre
     // no more); the main pass's other rows start empty.
     a.kc_rows = KC;
     DT_TRY(launch_tile_cc<DP>(a, kc_bucket(kmax + 1), MODE_SEED, NI, s));
+    if (qcap) {
+        DT_TRY(launch_query_cap<DP>(a, kmax, cap_leaves, qcap, s));
+        a.qcap = qcap;
+    }
     tm.mark();  // 1
 
     // 2. bounds of every query node down to the blocks
@@ -893,12 +899,12 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int pre
 
 // Shared option checks of dtree_knn and dtree_knn_batch.
 struct KnnOpts {
-    int prec, qb, seed_pts, spin, nprop;
+    int prec, qb, seed_pts, cap, spin, nprop;
 };
 
 int parse_opts(const dtree_opts* o, KnnOpts* ko) {
     if (o)
-        for (int i = 0; i < 10; ++i)
+        for (int i = 0; i < 9; ++i)
             if (o->reserved[i]) return DTREE_ERR_INVALID_ARG;
     ko->prec = o ? o->precision : DTREE_PREC_FP32;
     if (ko->prec < DTREE_PREC_FP32 || ko->prec > DTREE_PREC_BF16) return DTREE_ERR_INVALID_ARG;
@@ -906,7 +912,10 @@ int parse_opts(const dtree_opts* o, KnnOpts* ko) {
     if (ko->qb < 16 || ko->qb > 128) return DTREE_ERR_INVALID_ARG;
     ko->nprop = o ? o->proposal : 0;
     if (ko->nprop < 0 || ko->nprop > 8) return DTREE_ERR_INVALID_ARG;
-    ko->seed_pts = (o && o->seed_points > 0) ? o->seed_points : 512;
+    ko->seed_pts = (o && o->seed_points > 0) ? o->seed_points : 64;
+    ko->cap = (o && o->cap_leaves) ? o->cap_leaves : 8;
+    if (ko->cap < -1 || ko->cap > 17) return DTREE_ERR_INVALID_ARG;
+    if (ko->cap < 0) ko->cap = 0;
     ko->spin = (o && o->spin_budget > 0) ? o->spin_budget : (1 << 20);
     return DTREE_OK;
 }
@@ -939,11 +948,11 @@ int run_group(int dp, const HostProb* hp, int np, const KnnOpts& ko, cudaStream_
             if (!hp[i].prop) return DTREE_ERR_NOT_TRAINED;
     }
     switch (dp) {
-        case 4: return knn_batch_impl<4>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, ko.nprop, s, st, arena);
-        case 8: return knn_batch_impl<8>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, ko.nprop, s, st, arena);
-        case 16: return knn_batch_impl<16>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, ko.nprop, s, st, arena);
-        case 32: return knn_batch_impl<32>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, ko.nprop, s, st, arena);
-        default: return knn_batch_impl<64>(hp, np, ko.qb, ko.seed_pts, ko.prec, ko.spin, ko.nprop, s, st, arena);
+        case 4: return knn_batch_impl<4>(hp, np, ko.qb, ko.seed_pts, ko.cap, ko.prec, ko.spin, ko.nprop, s, st, arena);
+        case 8: return knn_batch_impl<8>(hp, np, ko.qb, ko.seed_pts, ko.cap, ko.prec, ko.spin, ko.nprop, s, st, arena);
+        case 16: return knn_batch_impl<16>(hp, np, ko.qb, ko.seed_pts, ko.cap, ko.prec, ko.spin, ko.nprop, s, st, arena);
+        case 32: return knn_batch_impl<32>(hp, np, ko.qb, ko.seed_pts, ko.cap, ko.prec, ko.spin, ko.nprop, s, st, arena);
+        default: return knn_batch_impl<64>(hp, np, ko.qb, ko.seed_pts, ko.cap, ko.prec, ko.spin, ko.nprop, s, st, arena);
     }
 }
 

@@ -86,6 +86,7 @@ struct TileArgs {
     float* cand_d;
     int32_t* cand_i;
     float* qub;                 // per query: upper bound on its true k-th distance (seed pass)
+    const float* qcap;          // per query: the cap pass's upper bound on it (or null)
     int* work_ctr;
     int4* fbq_list;    // queries whose error band overflowed: (tree position, block, ub bits, 0)
     int* fbq_count;
@@ -96,6 +97,11 @@ struct TileArgs {
 
 template <int DP>
 int launch_tile_cc(const TileArgs& a, int kc, int mode, int items, cudaStream_t s);
+
+// Per-query caps on the k-th distance (writes qcap, lowers qub): a best-first
+// search of up to `budget` reference leaves per query; kmax <= 63.
+template <int DP>
+int launch_query_cap(const TileArgs& a, int kmax, int budget, float* qcap, cudaStream_t s);
 
 template <int DP>
 int launch_query_fb(const TileArgs& a, int kc, int nfbq, bool exact, cudaStream_t s);

@@ -368,6 +368,8 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
         const bool mono = P.mono != 0;
         const float lam2 = 2.f * P.qlam[qnode];
         float qa = 0.f, qn = 0.f;
+        // the cap pass's bound on the query's k-th distance (main pass only)
+        const float qc = MODE == MODE_MAIN && act && a.qcap ? a.qcap[P.q0 + myq] : INFINITY;
         float ld[KC];
         int li[KC];
         if (role < 2) {
@@ -405,7 +407,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                     li[j] = a.cand_i[(int64_t)j * a.nq_all + (P.q0 + myq)];
                 }
             }
-            float ub = Bd::ub(list_at(ld, kq - 1), qa);
+            float ub = fminf(Bd::ub(list_at(ld, kq - 1), qa), qc);
             float vmax = act ? ub : -INFINITY, vmin = act ? ub : INFINITY;
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
@@ -738,7 +740,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                     // inside the error band of the current k-th key (a key above
                     // the band can never be a true k-nearest neighbour)
                     auto threshold = [&]() {
-                        const float bnd = Bd::band(Bd::ub(list_at(ld, kq - 1), qa), qa);
+                        const float bnd = Bd::band(fminf(Bd::ub(list_at(ld, kq - 1), qa), qc), qa);
                         return __fsub_ru(fminf(ld[KC - 1], bnd), qn);
                     };
                     float t = threshold();
@@ -828,7 +830,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                     atomicAdd(&x.timers[TT_EPI_WORK], (unsigned long long)(clock64() - te1));
                 if (!__any_sync(0xffffffffu, changed)) continue;  // the published bound stands
                 long long tb0 = clock64();
-                float ub = Bd::ub(list_at(ld, kq - 1), qa);
+                float ub = fminf(Bd::ub(list_at(ld, kq - 1), qa), qc);
                 float vmax = act ? ub : -INFINITY, vmin = act ? ub : INFINITY;
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) {
@@ -876,7 +878,7 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                         a.qub[P.q0 + myq] = Bd::ub(list_at(ld, kq - 1), qa);
                     }
                 } else {
-                    const float ubk = Bd::ub(list_at(ld, kq - 1), qa);
+                    const float ubk = fminf(Bd::ub(list_at(ld, kq - 1), qa), qc);
                     const float band = Bd::band(ubk, qa);
                     const bool ovf = act && li[KC - 1] != kEmptyIdx && !(ld[KC - 1] > band);
                     // the re-rank below reuses the merge buffers: all of group 0 has read them

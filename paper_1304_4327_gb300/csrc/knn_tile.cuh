@@ -247,10 +247,12 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
             }
             const float lam2 = 2.f * P.qlam[qnode];
             const float Bq = a.Bn ? a.Bn[P.node0 + qnode] : INFINITY;
+            // the cap pass's bound on the query's k-th distance (main pass only)
+            const float qc = MODE == MODE_MAIN && act && a.qcap ? a.qcap[row] : INFINITY;
 
             // the block's live bound: min(B from the traversal, B_1, B_2)
             auto refresh_bound = [&]() {
-                float ub = ub_of<T, DP>(list_at(ld, kq - 1));
+                float ub = fminf(ub_of<T, DP>(list_at(ld, kq - 1)), qc);
                 float vmax = act ? ub : -INFINITY, vmin = act ? ub : INFINITY;
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) {
@@ -655,6 +657,133 @@ template <class K>
 inline int tile_grid(K kern, int items) {
     int g = occupancy_grid((const void*)kern, kQB, 0);
     return items < g ? (items > 0 ? items : 1) : g;
+}
+
+// The cap pass: a budgeted best-first search of the reference tree for every
+// query.  From the root it walks down to a leaf, always into the child whose
+// box is nearer (the left one on a tie), queueing the farther child with its
+// box distance; it evaluates the leaf's points (itself excluded in a
+// monochromatic search) into a list of its KS smallest float32 distances,
+// then resumes from the nearest queued node, until it has evaluated `budget`
+// leaves or no queued box is nearer than its k-th distance.  Any k reference
+// points bound the true k-th-neighbour distance from above, so ub_of of the
+// list's k-th entry is a valid bound; it lowers the query's qub (so B of
+// Section 5 shrinks before the traversal) and caps the BaseCase's insertion
+// threshold.  Nothing else depends on these points: the BaseCase still
+// evaluates every candidate leaf.  The queue keeps its NPQ nearest entries,
+// enough for NPQ + 1 leaves (an entry beyond them is never reached in time).
+// One thread per query, one CTA per work item.
+template <int DP>
+__device__ __forceinline__ float point_box_d2f(const float* q, const float* bx) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < DP; ++j) {
+        const float g = fmaxf(fmaxf(bx[j] - q[j], q[j] - bx[DP + j]), 0.f);
+        s = fmaf(g, g, s);
+    }
+    return s;
+}
+
+constexpr int kCapQueue = 16;  // queued nodes, so at most 17 leaves per query
+
+template <int DP, int KS>
+__global__ void __launch_bounds__(kQB) k_query_cap(const TileArgs a, float* qcap, int budget) {
+    constexpr int NPQ = kCapQueue;
+    const int item = blockIdx.x;
+    if (item >= a.nitems) return;
+    const int2 wi = a.items[item];
+    const ProbDev& P = a.probs[a.blk_prob[wi.x]];
+    const int64_t qnode = P.qblock0 + (wi.x - P.block0);
+    const int nq = min(kQB, P.qcnt[qnode] - wi.y * kQB);
+    if ((int)threadIdx.x >= nq) return;
+    const int myq = P.qbeg[qnode] + wi.y * kQB + (int)threadIdx.x;
+    const int64_t row = P.q0 + myq;
+    const int kq = P.k, hr = P.hr;
+    const bool mono = P.mono != 0;
+    float q[DP];
+    {
+        const float4* q4 = reinterpret_cast<const float4*>(P.qpts + (int64_t)myq * DP);
+#pragma unroll
+        for (int j = 0; j < DP / 4; ++j) {
+            const float4 v = q4[j];
+            q[4 * j] = v.x;
+            q[4 * j + 1] = v.y;
+            q[4 * j + 2] = v.z;
+            q[4 * j + 3] = v.w;
+        }
+    }
+    float ld[KS];
+#pragma unroll
+    for (int j = 0; j < KS; ++j) ld[j] = INFINITY;
+    float pd[NPQ];
+    int32_t pn[NPQ];
+#pragma unroll
+    for (int j = 0; j < NPQ; ++j) {
+        pd[j] = INFINITY;
+        pn[j] = 0;
+    }
+    int64_t n = 0;
+    int lev = 0;
+    float kth = INFINITY;
+    for (int used = 0;;) {
+        for (; lev < hr; ++lev) {
+            const int64_t l = 2 * n + 1;
+            const float dl = point_box_d2f<DP>(q, P.rbox + l * 2 * DP);
+            const float dr = point_box_d2f<DP>(q, P.rbox + (l + 1) * 2 * DP);
+            const bool right = dr < dl;
+            const float df = right ? dl : dr;
+            if (df < kth && df < pd[NPQ - 1]) {
+                // sorted insertion of the farther child
+                const int32_t nf = (int32_t)(right ? l : l + 1);
+                bool le[NPQ];
+#pragma unroll
+                for (int j = 0; j < NPQ; ++j) le[j] = pd[j] <= df;
+#pragma unroll
+                for (int j = NPQ - 1; j >= 0; --j)
+                    if (!le[j]) {
+                        const bool here = j == 0 || le[j - 1];
+                        pd[j] = here ? df : pd[j - 1];
+                        pn[j] = here ? nf : pn[j - 1];
+                    }
+            }
+            n = right ? l + 1 : l;
+        }
+        const int rb = P.rbeg[n], rc = P.rcnt[n];
+        for (int r = rb; r < rb + rc; ++r) {
+            if (mono && r == myq) continue;
+            const float d = approx_d2<DP>(q, P.rpts + (int64_t)r * DP);
+            if (!(d < ld[KS - 1])) continue;
+            bool le[KS];
+#pragma unroll
+            for (int j = 0; j < KS; ++j) le[j] = ld[j] <= d;
+#pragma unroll
+            for (int j = KS - 1; j >= 0; --j)
+                if (!le[j]) ld[j] = (j == 0 || le[j - 1]) ? d : ld[j - 1];
+        }
+        kth = list_at(ld, kq - 1);
+        if (++used >= budget || !(pd[0] < kth)) break;
+        // resume from the nearest queued node
+        n = pn[0];
+        lev = 63 - __clzll((long long)n + 1);
+#pragma unroll
+        for (int j = 0; j + 1 < NPQ; ++j) {
+            pd[j] = pd[j + 1];
+            pn[j] = pn[j + 1];
+        }
+        pd[NPQ - 1] = INFINITY;
+    }
+    const float cap = ub_of<float, DP>(kth);
+    qcap[row] = cap;
+    a.qub[row] = fminf(a.qub[row], cap);
+}
+
+template <int DP>
+int launch_query_cap(const TileArgs& a, int kmax, int budget, float* qcap, cudaStream_t s) {
+    if (a.nitems <= 0) return DTREE_OK;
+    if (kmax > 64 || budget < 1) return DTREE_ERR_UNSUPPORTED;
+    auto kern = kmax <= 16 ? k_query_cap<DP, 16> : kmax <= 32 ? k_query_cap<DP, 32> : k_query_cap<DP, 64>;
+    DT_LAUNCH(kern, a.nitems, kQB, 0, s, a, qcap, std::min(budget, kCapQueue + 1));
+    return DTREE_OK;
 }
 
 template <int DP>

@@ -3,4 +3,5 @@
 
 namespace dt {
 template int launch_tile_cc<32>(const TileArgs&, int, int, int, cudaStream_t);
+template int launch_query_cap<32>(const TileArgs&, int, int, float*, cudaStream_t);
 }  // namespace dt
