@@ -101,10 +101,11 @@ class Autotuner:
 
 
 def run_batch(problems: Sequence[Tuple[object, Optional[object], int]], precision: str = "fp32",
-              tuner: Optional[Autotuner] = None):
+              tuner: Optional[Autotuner] = None, **knn_opts):
     """Build every problem's trees with its tuned leaf size and answer all of
     them in one dtree_knn_batch call with their tuned block sizes.
-    ``problems``: (ref points, query points or None, k) device tensors.
+    ``problems``: (ref points, query points or None, k) device tensors;
+    ``knn_opts`` go to dtree_knn_batch (seed_points, cap_leaves, ...).
     Returns one (idx, dist) pair per problem."""
     from . import dtree as dt
     tuner = tuner or Autotuner()
@@ -115,7 +116,7 @@ def run_batch(problems: Sequence[Tuple[object, Optional[object], int]], precisio
             tr = dt.dtree_build(ref, leaf)
             tq = None if query is None else dt.dtree_build(query, leaf)
             trees.append((tq, tr, k, qb))
-        return dt.dtree_knn_batch(trees, precision=precision)
+        return dt.dtree_knn_batch(trees, precision=precision, **knn_opts)
     finally:
         for tq, tr, _, _ in trees:
             tr.free()
