@@ -715,7 +715,7 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int cap
     a.kc_rows = KC;
     DT_TRY(launch_tile_cc<DP>(a, kc_bucket(kmax + 1), MODE_SEED, NI, s));
     if (qcap) {
-        DT_TRY(launch_query_cap<DP>(a, kmax, cap_leaves, qcap, s));
+        DT_TRY(launch_query_cap<DP>(a, KC, cap_leaves, qcap, s));
         a.qcap = qcap;
     }
     tm.mark();  // 1

@@ -98,10 +98,11 @@ struct TileArgs {
 template <int DP>
 int launch_tile_cc(const TileArgs& a, int kc, int mode, int items, cudaStream_t s);
 
-// Per-query caps on the k-th distance (writes qcap, lowers qub): a best-first
-// search of up to `budget` reference leaves per query; kmax <= 63.
+// Per-query caps on the k-th distance: a best-first search of up to `budget`
+// reference leaves per query, merged into its candidate list of kc (=
+// a.kc_rows) entries; writes qcap and lowers qub.
 template <int DP>
-int launch_query_cap(const TileArgs& a, int kmax, int budget, float* qcap, cudaStream_t s);
+int launch_query_cap(const TileArgs& a, int kc, int budget, float* qcap, cudaStream_t s);
 
 template <int DP>
 int launch_query_fb(const TileArgs& a, int kc, int nfbq, bool exact, cudaStream_t s);

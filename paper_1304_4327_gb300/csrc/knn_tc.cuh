@@ -754,7 +754,9 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                         for (int e = 0; e < nb; ++e) {
                             const float sv = qn + bw[e * kQB];
                             const int rp = bi[e * kQB];
-                            if (key_less(sv, rp, ld[KC - 1], li[KC - 1]) && !(mono && rp == myq)) {
+                            // (the cap pass may have listed this point already)
+                            if (key_less(sv, rp, ld[KC - 1], li[KC - 1]) && !(mono && rp == myq) &&
+                                !(MODE == MODE_MAIN && listed(li, rp))) {
                                 // the band moves only when the k-th key does
                                 const bool kth_moves = key_less(sv, rp, list_at(ld, kq - 1),
                                                                 list_at(li, kq - 1));

@@ -71,6 +71,15 @@ __device__ __forceinline__ void list_insert_par(T (&ld)[KC], int (&li)[KC], T d,
     }
 }
 
+// Is i among the list's indices?
+template <int KC>
+__device__ __forceinline__ bool listed(const int (&li)[KC], int i) {
+    bool in = false;
+#pragma unroll
+    for (int j = 0; j < KC; ++j) in |= li[j] == i;
+    return in;
+}
+
 template <typename T, int KC>
 __device__ __forceinline__ T list_at(const T (&ld)[KC], int j) {
     T v = ld[0];
@@ -338,7 +347,9 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
                             }
                             const int rp = spos[e];
                             const int tie = rp;
-                            if (key_less(acc, tie, ld[KC - 1], li[KC - 1]) && !(mono && rp == myq))
+                            // (the cap pass may have listed this point already)
+                            if (key_less(acc, tie, ld[KC - 1], li[KC - 1]) && !(mono && rp == myq) &&
+                                !(MODE == MODE_MAIN && listed(li, tie)))
                                 list_insert(ld, li, acc, tie);
                         }
                     }
@@ -660,19 +671,21 @@ inline int tile_grid(K kern, int items) {
 }
 
 // The cap pass: a budgeted best-first search of the reference tree for every
-// query.  From the root it walks down to a leaf, always into the child whose
-// box is nearer (the left one on a tie), queueing the farther child with its
-// box distance; it evaluates the leaf's points (itself excluded in a
-// monochromatic search) into a list of its KS smallest float32 distances,
-// then resumes from the nearest queued node, until it has evaluated `budget`
-// leaves or no queued box is nearer than its k-th distance.  Any k reference
-// points bound the true k-th-neighbour distance from above, so ub_of of the
-// list's k-th entry is a valid bound; it lowers the query's qub (so B of
-// Section 5 shrinks before the traversal) and caps the BaseCase's insertion
-// threshold.  Nothing else depends on these points: the BaseCase still
-// evaluates every candidate leaf.  The queue keeps its NPQ nearest entries,
-// enough for NPQ + 1 leaves (an entry beyond them is never reached in time).
-// One thread per query, one CTA per work item.
+// query, merged into the query's candidate list.  The list starts as the
+// seed pass left it.  From the root the search walks down to a leaf, always
+// into the child whose box is nearer (the left one on a tie), queueing the
+// farther child with its box distance; it offers the leaf's points (itself
+// excluded in a monochromatic search, points already listed skipped) to the
+// list with their float32 keys, the seed pass's keys, then resumes from the
+// nearest queued node, until it has evaluated `budget` leaves or no queued
+// box is nearer than the list's k-th key.  The list goes back to cand_d /
+// cand_i, and ub_of of its k-th key, a valid bound on the true k-th
+// distance, lowers the query's qub (so B of Section 5 shrinks before the
+// traversal) and caps the BaseCase's thresholds.  The BaseCase still
+// evaluates every candidate leaf, these included: its insertions skip
+// points already listed.  The queue keeps its NPQ nearest entries, enough
+// for NPQ + 1 leaves (an entry beyond them is never reached in time).  One
+// thread per query, one CTA per work item.
 template <int DP>
 __device__ __forceinline__ float point_box_d2f(const float* q, const float* bx) {
     float s = 0.f;
@@ -686,7 +699,7 @@ __device__ __forceinline__ float point_box_d2f(const float* q, const float* bx) 
 
 constexpr int kCapQueue = 16;  // queued nodes, so at most 17 leaves per query
 
-template <int DP, int KS>
+template <int DP, int KC>
 __global__ void __launch_bounds__(kQB) k_query_cap(const TileArgs a, float* qcap, int budget) {
     constexpr int NPQ = kCapQueue;
     const int item = blockIdx.x;
@@ -712,9 +725,13 @@ __global__ void __launch_bounds__(kQB) k_query_cap(const TileArgs a, float* qcap
             q[4 * j + 3] = v.w;
         }
     }
-    float ld[KS];
+    float ld[KC];
+    int li[KC];
 #pragma unroll
-    for (int j = 0; j < KS; ++j) ld[j] = INFINITY;
+    for (int j = 0; j < KC; ++j) {
+        ld[j] = a.cand_d[(int64_t)j * a.nq_all + row];
+        li[j] = a.cand_i[(int64_t)j * a.nq_all + row];
+    }
     float pd[NPQ];
     int32_t pn[NPQ];
 #pragma unroll
@@ -724,7 +741,7 @@ __global__ void __launch_bounds__(kQB) k_query_cap(const TileArgs a, float* qcap
     }
     int64_t n = 0;
     int lev = 0;
-    float kth = INFINITY;
+    float kth = list_at(ld, kq - 1);
     for (int used = 0;;) {
         for (; lev < hr; ++lev) {
             const int64_t l = 2 * n + 1;
@@ -752,13 +769,8 @@ __global__ void __launch_bounds__(kQB) k_query_cap(const TileArgs a, float* qcap
         for (int r = rb; r < rb + rc; ++r) {
             if (mono && r == myq) continue;
             const float d = approx_d2<DP>(q, P.rpts + (int64_t)r * DP);
-            if (!(d < ld[KS - 1])) continue;
-            bool le[KS];
-#pragma unroll
-            for (int j = 0; j < KS; ++j) le[j] = ld[j] <= d;
-#pragma unroll
-            for (int j = KS - 1; j >= 0; --j)
-                if (!le[j]) ld[j] = (j == 0 || le[j - 1]) ? d : ld[j - 1];
+            if (!key_less(d, r, ld[KC - 1], li[KC - 1]) || listed(li, r)) continue;
+            list_insert_par(ld, li, d, r);
         }
         kth = list_at(ld, kq - 1);
         if (++used >= budget || !(pd[0] < kth)) break;
@@ -772,18 +784,39 @@ __global__ void __launch_bounds__(kQB) k_query_cap(const TileArgs a, float* qcap
         }
         pd[NPQ - 1] = INFINITY;
     }
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+        a.cand_d[(int64_t)j * a.nq_all + row] = ld[j];
+        a.cand_i[(int64_t)j * a.nq_all + row] = li[j];
+    }
     const float cap = ub_of<float, DP>(kth);
     qcap[row] = cap;
     a.qub[row] = fminf(a.qub[row], cap);
 }
 
 template <int DP>
-int launch_query_cap(const TileArgs& a, int kmax, int budget, float* qcap, cudaStream_t s) {
+int launch_query_cap(const TileArgs& a, int kc, int budget, float* qcap, cudaStream_t s) {
     if (a.nitems <= 0) return DTREE_OK;
-    if (kmax > 64 || budget < 1) return DTREE_ERR_UNSUPPORTED;
-    auto kern = kmax <= 16 ? k_query_cap<DP, 16> : kmax <= 32 ? k_query_cap<DP, 32> : k_query_cap<DP, 64>;
-    DT_LAUNCH(kern, a.nitems, kQB, 0, s, a, qcap, std::min(budget, kCapQueue + 1));
-    return DTREE_OK;
+    if (budget < 1 || kc != a.kc_rows) return DTREE_ERR_UNSUPPORTED;
+    budget = std::min(budget, kCapQueue + 1);
+#define DT_CAP_CASE(KCV)                                                   \
+    case KCV: {                                                            \
+        auto kern = k_query_cap<DP, KCV>;                                  \
+        DT_LAUNCH(kern, a.nitems, kQB, 0, s, a, qcap, budget);             \
+        return DTREE_OK;                                                   \
+    }
+    switch (kc) {
+        DT_CAP_CASE(4)
+        DT_CAP_CASE(8)
+        DT_CAP_CASE(16)
+        DT_CAP_CASE(24)
+        DT_CAP_CASE(32)
+        DT_CAP_CASE(48)
+        DT_CAP_CASE(64)
+        default:
+            return DTREE_ERR_UNSUPPORTED;
+    }
+#undef DT_CAP_CASE
 }
 
 template <int DP>
