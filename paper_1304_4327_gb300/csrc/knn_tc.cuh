@@ -235,6 +235,8 @@ enum TcTimer {
     TT_TILES,            // converters: tiles produced
     TT_ITEMS,            // items processed
     TT_INSERTS,          // epilogue (all threads): candidate-list insertions
+    TT_EPI_WAIT_OP,      // epilogue (warp 0): of TT_EPI_WAIT, waiting for the operand slot
+    TT_EPI_WAIT_BAR,     // epilogue (warp 0): of TT_EPI_WAIT, the group barrier before the MMA
     TT_N
 };
 static_assert(TT_N <= 32, "the diagnostic timer buffer holds 32 counters");
@@ -686,11 +688,17 @@ __global__ void __launch_bounds__(384, 1) k_tile_tc(const TileArgs a, const TcEx
                 bool ok = tc::mbar_wait(&op_full[op], ouse & 1u, x.spin_budget);
                 if (!__all_sync(0xffffffffu, ok) && lane == 0) s_gfail[role] = 1;
                 const int nst = ok ? ometa[op] : -1;
+                long long tw1 = clock64();
                 // every warp of the group is done with the last tile (its TMEM
                 // reads and its column positions) before either is replaced
                 tc::fence_before_sync();
                 tc::named_sync(gbar, 128);
                 tc::fence_after_sync();
+                if (x.timers && (warp & 3) == 0 && lane == 0) {
+                    const long long tw2 = clock64();
+                    atomicAdd(&x.timers[TT_EPI_WAIT_OP], (unsigned long long)(tw1 - te0));
+                    atomicAdd(&x.timers[TT_EPI_WAIT_BAR], (unsigned long long)(tw2 - tw1));
+                }
                 if (s_gfail[role]) {
                     s_fail = 1;
                     break;

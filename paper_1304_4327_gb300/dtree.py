@@ -408,7 +408,7 @@ def dtree_debug_mma(A: torch.Tensor, B: torch.Tensor, fmt: str = "bf16", stream=
 TC_TIMERS = ("plan_window", "plan_wait", "plan_stage", "conv_wait_raw", "conv_wait_slot",
              "conv_work", "epi_wait", "epi_work", "epi_rare_chunks", "epi_finish", "item_setup",
              "epi_tmem", "epi_hot", "epi_rare_cycles", "epi_tail", "epi_flush", "tiles", "items",
-             "inserts")
+             "inserts", "epi_wait_op", "epi_wait_bar")
 
 
 def dtree_debug_tc_timers(buf: Optional[torch.Tensor]) -> None:
