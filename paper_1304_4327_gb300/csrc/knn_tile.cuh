@@ -671,134 +671,218 @@ inline int tile_grid(K kern, int items) {
 }
 
 // The cap pass: a budgeted best-first search of the reference tree for every
-// query, merged into the query's candidate list.  The list starts as the
-// seed pass left it.  From the root the search walks down to a leaf, always
-// into the child whose box is nearer (the left one on a tie), queueing the
-// farther child with its box distance; it offers the leaf's points (itself
-// excluded in a monochromatic search, points already listed skipped) to the
-// list with their float32 keys, the seed pass's keys, then resumes from the
-// nearest queued node, until it has evaluated `budget` leaves or no queued
-// box is nearer than the list's k-th key.  The list goes back to cand_d /
-// cand_i, and ub_of of its k-th key, a valid bound on the true k-th
-// distance, lowers the query's qub (so B of Section 5 shrinks before the
-// traversal) and caps the BaseCase's thresholds.  The BaseCase still
-// evaluates every candidate leaf, these included: its insertions skip
-// points already listed.  The queue keeps its NPQ nearest entries, enough
-// for NPQ + 1 leaves (an entry beyond them is never reached in time).  One
-// thread per query, one CTA per work item.
-template <int DP>
-__device__ __forceinline__ float point_box_d2f(const float* q, const float* bx) {
-    float s = 0.f;
-#pragma unroll
-    for (int j = 0; j < DP; ++j) {
-        const float g = fmaxf(fmaxf(bx[j] - q[j], q[j] - bx[DP + j]), 0.f);
-        s = fmaf(g, g, s);
-    }
-    return s;
-}
-
-constexpr int kCapQueue = 16;  // queued nodes, so at most 17 leaves per query
+// query, merged into the query's candidate list.  One warp serves one query
+// at a time.  The list starts as the seed pass left it.  From the root the
+// search walks down to a leaf, always into the child whose box is nearer
+// (the left one on a tie), queueing the farther child with its box
+// distance; it offers the leaf's points (itself excluded in a monochromatic
+// search) to the list with their float32 keys, the seed pass's keys, then
+// resumes from the nearest queued node, until it has evaluated `budget`
+// leaves or no queued box is nearer than the list's k-th key.  The block's
+// seed leaves are skipped (the seed pass offered their points already), and
+// no leaf is reached twice, so no point enters the list twice.  The list
+// goes back to cand_d / cand_i, and ub_of of its k-th key, a valid bound on
+// the true k-th distance, lowers the query's qub (so B of Section 5 shrinks
+// before the traversal) and caps the BaseCase's thresholds.  The BaseCase
+// still evaluates every candidate leaf, these included: its insertions skip
+// points already listed.
+//
+// Lane layout: list entry 32 s + lane in (ld[s], li[s]); queue entry `lane`
+// in (pd, pn), ascending (32 entries, more than a budget can reach); box
+// element e = lane + 32 t of the two children (child e / DP, coordinate
+// e % DP), whose query coordinate is qd[t]; point rb + lane (+ 32 u) of a leaf.
+constexpr int kCapMaxLeaves = 17;
 
 template <int DP, int KC>
 __global__ void __launch_bounds__(kQB) k_query_cap(const TileArgs a, float* qcap, int budget) {
-    constexpr int NPQ = kCapQueue;
+    constexpr int NE = (KC + 31) / 32;      // list entries per lane
+    constexpr int NT = (2 * DP + 31) / 32;  // box elements per lane
     const int item = blockIdx.x;
     if (item >= a.nitems) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int2 wi = a.items[item];
-    const ProbDev& P = a.probs[a.blk_prob[wi.x]];
-    const int64_t qnode = P.qblock0 + (wi.x - P.block0);
+    const int blk = wi.x;
+    const ProbDev& P = a.probs[a.blk_prob[blk]];
+    const int64_t qnode = P.qblock0 + (blk - P.block0);
     const int nq = min(kQB, P.qcnt[qnode] - wi.y * kQB);
-    if ((int)threadIdx.x >= nq) return;
-    const int myq = P.qbeg[qnode] + wi.y * kQB + (int)threadIdx.x;
-    const int64_t row = P.q0 + myq;
     const int kq = P.k, hr = P.hr;
     const bool mono = P.mono != 0;
-    float q[DP];
-    {
-        const float4* q4 = reinterpret_cast<const float4*>(P.qpts + (int64_t)myq * DP);
+    for (int qi = warp; qi < nq; qi += kQB / 32) {
+        const int myq = P.qbeg[qnode] + wi.y * kQB + qi;
+        const int64_t row = P.q0 + myq;
+        const float* qp = P.qpts + (int64_t)myq * DP;
+        float q[DP];
 #pragma unroll
         for (int j = 0; j < DP / 4; ++j) {
-            const float4 v = q4[j];
+            const float4 v = reinterpret_cast<const float4*>(qp)[j];
             q[4 * j] = v.x;
             q[4 * j + 1] = v.y;
             q[4 * j + 2] = v.z;
             q[4 * j + 3] = v.w;
         }
-    }
-    float ld[KC];
-    int li[KC];
+        float qd[NT];
 #pragma unroll
-    for (int j = 0; j < KC; ++j) {
-        ld[j] = a.cand_d[(int64_t)j * a.nq_all + row];
-        li[j] = a.cand_i[(int64_t)j * a.nq_all + row];
-    }
-    float pd[NPQ];
-    int32_t pn[NPQ];
+        for (int t = 0; t < NT; ++t) {
+            const int e = lane + 32 * t;
+            qd[t] = e < 2 * DP ? qp[e % DP] : 0.f;
+        }
+        float ld[NE];
+        int li[NE];
 #pragma unroll
-    for (int j = 0; j < NPQ; ++j) {
-        pd[j] = INFINITY;
-        pn[j] = 0;
-    }
-    int64_t n = 0;
-    int lev = 0;
-    float kth = list_at(ld, kq - 1);
-    for (int used = 0;;) {
-        for (; lev < hr; ++lev) {
-            const int64_t l = 2 * n + 1;
-            const float dl = point_box_d2f<DP>(q, P.rbox + l * 2 * DP);
-            const float dr = point_box_d2f<DP>(q, P.rbox + (l + 1) * 2 * DP);
-            const bool right = dr < dl;
-            const float df = right ? dl : dr;
-            if (df < kth && df < pd[NPQ - 1]) {
-                // sorted insertion of the farther child
-                const int32_t nf = (int32_t)(right ? l : l + 1);
-                bool le[NPQ];
+        for (int s = 0; s < NE; ++s) {
+            const int e = 32 * s + lane;
+            ld[s] = e < KC ? a.cand_d[(int64_t)e * a.nq_all + row] : INFINITY;
+            li[s] = e < KC ? a.cand_i[(int64_t)e * a.nq_all + row] : kEmptyIdx;
+        }
+        // list entry e (uniform e), broadcast to the warp
+        auto entry_d = [&](int e) {
+            float v = ld[0];
 #pragma unroll
-                for (int j = 0; j < NPQ; ++j) le[j] = pd[j] <= df;
+            for (int s = 1; s < NE; ++s)
+                if ((e >> 5) == s) v = ld[s];
+            return __shfl_sync(0xffffffffu, v, e & 31);
+        };
+        auto entry_i = [&](int e) {
+            int v = li[0];
 #pragma unroll
-                for (int j = NPQ - 1; j >= 0; --j)
-                    if (!le[j]) {
-                        const bool here = j == 0 || le[j - 1];
-                        pd[j] = here ? df : pd[j - 1];
-                        pn[j] = here ? nf : pn[j - 1];
+            for (int s = 1; s < NE; ++s)
+                if ((e >> 5) == s) v = li[s];
+            return __shfl_sync(0xffffffffu, v, e & 31);
+        };
+        float pd = INFINITY;
+        int32_t pn = 0;
+        int64_t n = 0;
+        int lev = 0;
+        float kth = entry_d(kq - 1);
+        for (int used = 0;;) {
+            for (; lev < hr; ++lev) {
+                const int64_t l = 2 * n + 1;
+                const float* bx = P.rbox + l * 2 * DP;  // the boxes of children l and l + 1
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    const int e = lane + 32 * t;
+                    if (e < 2 * DP) {
+                        const int c = e / DP, d = e % DP;
+                        const float g = fmaxf(fmaxf(bx[c * 2 * DP + d] - qd[t], qd[t] - bx[c * 2 * DP + DP + d]), 0.f);
+                        if (c == 0) s0 = fmaf(g, g, s0);
+                        else s1 = fmaf(g, g, s1);
                     }
+                }
+                float dl, dr;
+                if (2 * DP <= 32) {
+                    // child c's coordinates sit in lanes [c DP, c DP + DP)
+                    float sv = s0 + s1;
+#pragma unroll
+                    for (int off = DP / 2; off > 0; off >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, off);
+                    dl = __shfl_sync(0xffffffffu, sv, 0);
+                    dr = __shfl_sync(0xffffffffu, sv, DP);
+                } else {
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+                        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+                    }
+                    dl = s0;
+                    dr = s1;
+                }
+                const bool right = dr < dl;
+                const float df = right ? dl : dr;
+                if (df < kth) {
+                    // sorted insertion of the farther child (the last entry drops)
+                    const int32_t nf = (int32_t)(right ? l : l + 1);
+                    const int pos = __popc(__ballot_sync(0xffffffffu, pd <= df));
+                    const float upd = __shfl_up_sync(0xffffffffu, pd, 1);
+                    const int32_t upn = __shfl_up_sync(0xffffffffu, pn, 1);
+                    if (lane > pos) {
+                        pd = upd;
+                        pn = upn;
+                    } else if (lane == pos) {
+                        pd = df;
+                        pn = nf;
+                    }
+                }
+                n = right ? l + 1 : l;
             }
-            n = right ? l + 1 : l;
-        }
-        const int rb = P.rbeg[n], rc = P.rcnt[n];
-        for (int r = rb; r < rb + rc; ++r) {
-            if (mono && r == myq) continue;
-            const float d = approx_d2<DP>(q, P.rpts + (int64_t)r * DP);
-            if (!key_less(d, r, ld[KC - 1], li[KC - 1]) || listed(li, r)) continue;
-            list_insert_par(ld, li, d, r);
-        }
-        kth = list_at(ld, kq - 1);
-        if (++used >= budget || !(pd[0] < kth)) break;
-        // resume from the nearest queued node
-        n = pn[0];
-        lev = 63 - __clzll((long long)n + 1);
+            if (!in_seed(a.seed_leaf0, a.seed_nleaf, a.seed_slots, blk, (int)(n - P.rleaf0))) {
+                const int rb = P.rbeg[n], rc = P.rcnt[n];
+                float td = entry_d(KC - 1);
+                int ti = entry_i(KC - 1);
+                for (int r0 = 0; r0 < rc; r0 += 32) {
+                    const int r = rb + r0 + lane;
+                    float d = INFINITY;
+                    if (r0 + lane < rc && !(mono && r == myq)) d = approx_d2<DP>(q, P.rpts + (int64_t)r * DP);
+                    uint32_t m = __ballot_sync(0xffffffffu, d < INFINITY && key_less(d, r, td, ti));
+                    while (m) {
+                        const int src = __ffs(m) - 1;
+                        m &= m - 1;
+                        const float cd = __shfl_sync(0xffffffffu, d, src);
+                        const int ci = __shfl_sync(0xffffffffu, r, src);
+                        if (!key_less(cd, ci, td, ti)) continue;
+                        // insert (cd, ci): entries from its position on move up one
+                        int pos = 0;
 #pragma unroll
-        for (int j = 0; j + 1 < NPQ; ++j) {
-            pd[j] = pd[j + 1];
-            pn[j] = pn[j + 1];
-        }
-        pd[NPQ - 1] = INFINITY;
-    }
+                        for (int s = 0; s < NE; ++s)
+                            pos += __popc(__ballot_sync(0xffffffffu, key_less(ld[s], li[s], cd, ci)));
 #pragma unroll
-    for (int j = 0; j < KC; ++j) {
-        a.cand_d[(int64_t)j * a.nq_all + row] = ld[j];
-        a.cand_i[(int64_t)j * a.nq_all + row] = li[j];
+                        for (int s = NE - 1; s >= 0; --s) {
+                            float pv = __shfl_up_sync(0xffffffffu, ld[s], 1);
+                            int pi = __shfl_up_sync(0xffffffffu, li[s], 1);
+                            if (s > 0) {
+                                const float cv = __shfl_sync(0xffffffffu, ld[s > 0 ? s - 1 : 0], 31);
+                                const int cix = __shfl_sync(0xffffffffu, li[s > 0 ? s - 1 : 0], 31);
+                                if (lane == 0) {
+                                    pv = cv;
+                                    pi = cix;
+                                }
+                            }
+                            const int e = 32 * s + lane;
+                            if (e < KC) {
+                                if (e > pos) {
+                                    ld[s] = pv;
+                                    li[s] = pi;
+                                } else if (e == pos) {
+                                    ld[s] = cd;
+                                    li[s] = ci;
+                                }
+                            }
+                        }
+                        td = entry_d(KC - 1);
+                        ti = entry_i(KC - 1);
+                    }
+                }
+            }
+            kth = entry_d(kq - 1);
+            const float head = __shfl_sync(0xffffffffu, pd, 0);
+            if (++used >= budget || !(head < kth)) break;
+            // resume from the nearest queued node
+            n = __shfl_sync(0xffffffffu, pn, 0);
+            lev = 63 - __clzll((long long)n + 1);
+            pd = __shfl_down_sync(0xffffffffu, pd, 1);
+            pn = __shfl_down_sync(0xffffffffu, pn, 1);
+            if (lane == 31) pd = INFINITY;
+        }
+#pragma unroll
+        for (int s = 0; s < NE; ++s) {
+            const int e = 32 * s + lane;
+            if (e < KC) {
+                a.cand_d[(int64_t)e * a.nq_all + row] = ld[s];
+                a.cand_i[(int64_t)e * a.nq_all + row] = li[s];
+            }
+        }
+        if (lane == 0) {
+            const float cap = ub_of<float, DP>(kth);
+            qcap[row] = cap;
+            a.qub[row] = fminf(a.qub[row], cap);
+        }
     }
-    const float cap = ub_of<float, DP>(kth);
-    qcap[row] = cap;
-    a.qub[row] = fminf(a.qub[row], cap);
 }
 
 template <int DP>
 int launch_query_cap(const TileArgs& a, int kc, int budget, float* qcap, cudaStream_t s) {
     if (a.nitems <= 0) return DTREE_OK;
     if (budget < 1 || kc != a.kc_rows) return DTREE_ERR_UNSUPPORTED;
-    budget = std::min(budget, kCapQueue + 1);
+    budget = std::min(budget, kCapMaxLeaves);
 #define DT_CAP_CASE(KCV)                                                   \
     case KCV: {                                                            \
         auto kern = k_query_cap<DP, KCV>;                                  \
