@@ -8,7 +8,8 @@ live in their own module and hold none of the method's arithmetic).
 The C source (``dtree_oracle.c``) is plain IEEE double precision compiled with
 ``-ffp-contract=off``; see its header for the paper passages and the readings
 of the paper it follows.  ``mlp.py`` holds the double-precision reference of
-the learned proposal's network.
+the learned proposal's network, and ``kfn.py`` the k-furthest-neighbour
+problem (its brute-force definition and the inverted dual-tree).
 """
 from __future__ import annotations
 
