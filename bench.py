@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--cpu-queries", type=int, default=8192)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ref-queries", type=int, default=512)
+    p.add_argument("--op", choices=["knn", "kfn"], default="knn",
+                   help="knn: the headline; kfn: exact k-furthest neighbours on the same workload")
     return p.parse_args()
 
 
@@ -251,6 +253,9 @@ def job_rate(world, n_per_rank, ms_max):
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.op == "kfn":
+        run_kfn(args, rank, world, local)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
@@ -368,6 +373,164 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W, args.cpu_queries)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# k-furthest neighbours (--op kfn): the same workload, the same contract
+# ---------------------------------------------------------------------------
+
+METRIC_KFN = "exact k-furthest-neighbour queries/s (oracle-identical)"
+WORKLOAD_KFN = WORKLOAD.replace("exact kNN", "exact k-furthest neighbours")
+
+
+def run_kfn(args, rank, world, local):
+    """One step = build the reference tree + build the query tree + dtree_kfn
+    (one warp per query: the single-tree depth-first search with the inverted
+    Score and BaseCase, float32 keys, float64 re-rank and fallback)."""
+    from oracle import kfn as okfn
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        W = inputs.gmm16(n_ref=args.n_ref, n_query=args.n_query)
+        nq = min(args.ref_queries, 16)
+        times = []
+        for step in range(args.warmup + args.steps):
+            lo = (step * nq) % max(1, len(W.query) - nq)
+            t0 = time.perf_counter()
+            okfn.kfn_brute(W.ref, W.query[lo:lo + nq], W.k)
+            if step >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        t = sum(times) / len(times)
+        value = nq / t
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC_KFN, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_KFN, "step": f"{nq}-query sample per step, brute force"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{nq} queries per step vs all {len(W.ref)} references, "
+                                       "float64 brute force (oracle.kfn.kfn_brute, numpy)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }), flush=True)
+        return
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1304_4327_gb300 import dtree
+    W = shard_workload(args, rank)
+    d, k = W.d, W.k
+    ref_d = torch.from_numpy(W.ref).cuda()
+    q_d = torch.from_numpy(W.query).cuda()
+    nq = q_d.shape[0]
+    out_idx = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    out_dist = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(ref, qry):
+        tr = dtree.dtree_build(ref, args.leaf)
+        tq = dtree.dtree_build(qry, args.leaf)
+        try:
+            _, _, st = dtree.dtree_kfn(tq, tr, k, out_idx=out_idx, out_dist=out_dist,
+                                       with_stats=True)
+        finally:
+            tr.free()
+            tq.free()
+        return st
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(ref_d, q_d)
+    props = torch.cuda.get_device_properties(local)
+    uuid = getattr(props, "uuid", None)
+    clocks = ClockSampler(f"GPU-{uuid}" if uuid else None)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = dtree.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = [step(ref_d, q_d) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clock_info = clocks.stop()
+    launches = dtree.launch_count() - launches0
+    ms_max = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
+    value = job_rate(world, nq, ms_max)
+    # end to end: pinned host inputs in, host results out
+    ref_h = torch.from_numpy(W.ref).pin_memory()
+    q_h = torch.from_numpy(W.query).pin_memory()
+    idx_h = torch.empty((nq, k), dtype=torch.int64).pin_memory()
+    dist_h = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+    ref_e, q_e = torch.empty_like(ref_d), torch.empty_like(q_d)
+    barrier()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.e2e_steps):
+        ref_e.copy_(ref_h, non_blocking=True)
+        q_e.copy_(q_h, non_blocking=True)
+        step(ref_e, q_e)
+        idx_h.copy_(out_idx, non_blocking=True)
+        dist_h.copy_(out_dist, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value = job_rate(world, nq, max_over_ranks(f0.elapsed_time(f1) / args.e2e_steps, world, "cuda"))
+    ns = sum(s["ns_basecase"] for s in stats) / len(stats)
+    pairs = sum(s["point_pairs"] for s in stats) / len(stats)
+    sms = props.multi_processor_count
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    flops = 3.0 * d * pairs  # d subtractions + d FMAs per point distance
+    peak = 2.0 * 128 * sms * sm_max * 1e6 / 1e12
+    achieved = flops / (ns * 1e-9) / 1e12 if ns > 0 else 0.0
+    s0 = stats[-1]
+    line = {
+        "metric": METRIC_KFN, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_KFN, "precision": "fp32 keys, f64 re-rank", "leaf_size": args.leaf,
+                   "step": "build ref tree + build query tree + dtree_kfn",
+                   "l2": "inputs (320 MB) larger than the 129 MB L2; no flush",
+                   "parallelism": f"{world} GPU(s), one query shard each, reference replicated"},
+        "roofline": {"bound": "alu", "kernel": "k_kfn (one warp per query, float32 keys)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "peak_source": f"2 x 128 FP32 lanes x {sms} SMs x {sm_max:.0f} MHz",
+                     "algorithmic_flops_per_step": flops, "point_pairs_per_step": pairs,
+                     "kernel_ms": ns / 1e6},
+        "phases_ms": {"kfn": ns / 1e6, "build_and_rest": ms_max - ns / 1e6},
+        "counters": {k2: s0[k2] for k2 in ("point_pairs", "leaf_pairs_evaluated",
+                                          "node_pairs_pruned", "fallback_queries")},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(W.ref.nbytes + W.query.nbytes),
+                "d2h_bytes_per_step": int(nq * k * (8 + 4))},
+        "gpu_launches": int(launches),
+        "clocks": clock_info,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nb = 16
+        t0 = time.perf_counter()
+        okfn.kfn_brute(W.ref, W.query[:nb], k)
+        dt_ = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": nb / dt_, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"float64 brute force (numpy, one thread) for the first {nb} "
+                                          f"queries against all {len(W.ref)} references; {dt_:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -160,6 +160,38 @@ int dtree_build(const float* pts, int64_t n, int32_t d, const dtree_opts* opts, 
 int dtree_knn(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_idx,
               float* out_dist, const dtree_opts* opts, void* stream, dtree_stats* stats);
 
+/*
+ * dtree_kfn -- exact k-furthest-neighbour search: for every query the k
+ * reference points at the LARGEST Euclidean distance (Section 5, the
+ * paragraph on k-furthest neighbour search after Algorithm 4: the kNN rules
+ * inverted -- lists by descending distance, a candidate kept when it is
+ * farther than the k-th, a node pruned when its farthest possible point is
+ * nearer than the k-th furthest so far).
+ *   query     query tree, or NULL (or == ref) for the monochromatic problem,
+ *             where a point never returns itself (by index)
+ *   ref       reference tree
+ *   k         1 <= k <= 63, and k < n_ref (k <= n_ref - 1 monochromatic)
+ *   out_idx   device, n_q x k int64, row-major in the caller's query order:
+ *             row indices into the caller's reference array, descending by
+ *             (distance), ties by the lower index
+ *   out_dist  device, n_q x k float32: the Euclidean distance, computed in
+ *             float64 and rounded once
+ *   opts      nullable; precision must be DTREE_PREC_FP32 (float32 keys with a
+ *             float64 re-rank, float64 keys for queries whose error band
+ *             overflows: results are exact either way); other fields ignored
+ *   stream    cudaStream_t or NULL
+ *   stats     nullable; point_pairs (point distances evaluated),
+ *             leaf_pairs_evaluated (leaves visited), node_pairs_pruned,
+ *             fallback_queries, kernel_launches, ns_basecase
+ * Status: DTREE_ERR_INVALID_ARG (null tree or outputs, dimension mismatch,
+ * trees on another device, non-zero reserved options), DTREE_ERR_INVALID_K,
+ * DTREE_ERR_UNSUPPORTED (k > 63, another precision, a reference tree deeper
+ * than 30 levels), or a CUDA error.  Waits for the result.  Scratch comes
+ * from the device's stream-ordered pool.
+ */
+int dtree_kfn(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_idx,
+              float* out_dist, const dtree_opts* opts, void* stream, dtree_stats* stats);
+
 /* One problem of a batch: the arguments of one dtree_knn call. */
 typedef struct dtree_problem {
     const dtree_t* query;   /* NULL (or == ref): monochromatic */

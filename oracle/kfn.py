@@ -70,7 +70,6 @@ def kfn_brute(ref: np.ndarray, query: Optional[np.ndarray], k: int,
         raise ValueError("k out of range")
     out_i = np.empty((n, k), dtype=np.int64)
     out_d = np.empty((n, k), dtype=np.float64)
-    ids = np.arange(m, dtype=np.int64)
     for c0 in range(0, n, chunk):
         D = _d2_rows(Q[c0:c0 + chunk], R)
         rows = np.arange(D.shape[0])
@@ -78,9 +77,14 @@ def kfn_brute(ref: np.ndarray, query: Optional[np.ndarray], k: int,
             s = np.asarray(self_idx[c0:c0 + chunk], dtype=np.int64)
             keep = s >= 0
             D[rows[keep], s[keep]] = -np.inf  # never selected: k <= m - 1
-        order = np.lexsort((np.broadcast_to(ids, D.shape), -D), axis=-1)[:, :k]
-        out_i[c0:c0 + D.shape[0]] = order
-        out_d[c0:c0 + D.shape[0]] = np.take_along_axis(D, order, axis=1)
+        # the k-th largest value of each row; every point at or above it is a
+        # candidate (ties included), ranked by (distance desc, index asc)
+        thr = -np.partition(-D, k - 1, axis=1)[:, k - 1]
+        for i in rows:
+            cand = np.nonzero(D[i] >= thr[i])[0]
+            order = cand[np.lexsort((cand, -D[i, cand]))][:k]
+            out_i[c0 + i] = order
+            out_d[c0 + i] = D[i, order]
     return out_i, out_d
 
 

@@ -87,6 +87,8 @@ def _load() -> ctypes.CDLL:
     lib.dtree_alloc_count.argtypes = []
     lib.dtree_alloc_count.restype = _I64
     lib.dtree_knn_noalloc.argtypes = [_P, _P, _I32, _P, _P, ctypes.POINTER(dtree_opts), _P]
+    lib.dtree_kfn.argtypes = [_P, _P, _I32, _P, _P, ctypes.POINTER(dtree_opts), _P,
+                              ctypes.POINTER(dtree_stats)]
     lib.dtree_knn_batch.argtypes = [_I32, ctypes.POINTER(dtree_problem), ctypes.POINTER(dtree_opts),
                                     _P, ctypes.POINTER(dtree_stats)]
     lib.dtree_proposal_train.argtypes = [_P, _P, _I32, ctypes.POINTER(dtree_train_opts), _P,
@@ -336,6 +338,37 @@ def dtree_mlp_loss_grad(params, X: torch.Tensor, T: torch.Tensor, stream=None):
 
 
 NOALLOC_MAX_QUERIES = 65536
+
+
+def dtree_kfn(query: Optional[Tree], ref: Tree, k: int, out_idx: Optional[torch.Tensor] = None,
+              out_dist: Optional[torch.Tensor] = None, stream=None, with_stats: bool = False,
+              precision: str = "fp32"):
+    """Exact k-furthest neighbours of every point of ``query`` (None =
+    monochromatic) in ``ref``: (idx int64 (n_q, k), dist float32 (n_q, k)) on
+    the device, descending by distance (ties by the lower index), plus a dict
+    of counters when ``with_stats``."""
+    nq = ref.n if query is None else query.n
+    dev = torch.device("cuda", torch.cuda.current_device())
+    kk = max(int(k), 0)
+    if out_idx is None:
+        out_idx = torch.empty((nq, kk), dtype=torch.int64, device=dev)
+    if out_dist is None:
+        out_dist = torch.empty((nq, kk), dtype=torch.float32, device=dev)
+    if out_idx.shape != (nq, kk) or out_idx.dtype != torch.int64 or not out_idx.is_contiguous():
+        raise ValueError("out_idx must be a contiguous int64 (n_q, k) tensor")
+    if out_dist.shape != (nq, kk) or out_dist.dtype != torch.float32 or not out_dist.is_contiguous():
+        raise ValueError("out_dist must be a contiguous float32 (n_q, k) tensor")
+    o = _opts(precision=PRECISIONS[precision])
+    st = dtree_stats()
+    rc = _lib.dtree_kfn(None if query is None else query.handle, ref.handle, int(k),
+                        ctypes.c_void_p(out_idx.data_ptr()) if out_idx.numel() else None,
+                        ctypes.c_void_p(out_dist.data_ptr()) if out_dist.numel() else None,
+                        ctypes.byref(o), _stream(stream), ctypes.byref(st) if with_stats else None)
+    if rc != DTREE_OK:
+        raise DTreeError(rc, "dtree_kfn")
+    if with_stats:
+        return out_idx, out_dist, {f: int(getattr(st, f)) for f in STAT_FIELDS}
+    return out_idx, out_dist
 
 
 def dtree_knn_noalloc(query: Optional[Tree], ref: Tree, k: int, out_idx: torch.Tensor,
