@@ -8,8 +8,10 @@ live in their own module and hold none of the method's arithmetic).
 The C source (``dtree_oracle.c``) is plain IEEE double precision compiled with
 ``-ffp-contract=off``; see its header for the paper passages and the readings
 of the paper it follows.  ``mlp.py`` holds the double-precision reference of
-the learned proposal's network, and ``kfn.py`` the k-furthest-neighbour
-problem (its brute-force definition and the inverted dual-tree).
+the learned proposal's network, ``kfn.py`` the k-furthest-neighbour problem
+(its brute-force definition and the inverted dual-tree), and
+``rangesearch.py`` range search (its definition and the dual-tree with the
+range Score).
 """
 from __future__ import annotations
 
