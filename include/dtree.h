@@ -192,6 +192,37 @@ int dtree_knn(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_
 int dtree_kfn(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_idx,
               float* out_dist, const dtree_opts* opts, void* stream, dtree_stats* stats);
 
+/*
+ * dtree_range_count / dtree_range_fill -- exact range search (Section 6): for
+ * every query all reference points with d_lo <= ||q - r|| <= d_hi, both ends
+ * inclusive, decided on the float64 distance (the correctly rounded square
+ * root of the float64 sum of squared float32 differences); a monochromatic
+ * query (query NULL or == ref) never returns itself.  Two calls, count then
+ * fill:
+ *   dtree_range_count writes offsets[0..n_q] (device, int64, n_q + 1):
+ *     query row i's neighbours will occupy [offsets[i], offsets[i + 1]) of
+ *     the outputs (rows in the caller's query order), and *total (host) gets
+ *     offsets[n_q]; stats (nullable): point_pairs (distances evaluated),
+ *     leaf_pairs_evaluated, node_pairs_pruned, rerank_candidates (points
+ *     decided in float64), kernel_launches, ns_basecase.
+ *   dtree_range_fill writes each query's segment: out_idx (device, int64,
+ *     *total) the caller's reference row indices, out_dist (device, float32)
+ *     the distances rounded once from float64.  Within a segment the order is
+ *     the search's visit order (the problem's lists are sets); it is the same
+ *     from call to call.
+ * The same trees and range must be passed to both.  opts: nullable,
+ * precision must be DTREE_PREC_FP32.  Status: DTREE_ERR_INVALID_ARG (null
+ * tree or buffer, dimension mismatch, d_lo < 0, d_hi < d_lo, NaN, trees on
+ * another device), DTREE_ERR_UNSUPPORTED (another precision, a reference tree
+ * deeper than 30 levels), or a CUDA error.  Both wait for the result.
+ */
+int dtree_range_count(const dtree_t* query, const dtree_t* ref, double d_lo, double d_hi,
+                      int64_t* offsets, int64_t* total, const dtree_opts* opts, void* stream,
+                      dtree_stats* stats);
+int dtree_range_fill(const dtree_t* query, const dtree_t* ref, double d_lo, double d_hi,
+                     const int64_t* offsets, int64_t* out_idx, float* out_dist,
+                     const dtree_opts* opts, void* stream);
+
 /* One problem of a batch: the arguments of one dtree_knn call. */
 typedef struct dtree_problem {
     const dtree_t* query;   /* NULL (or == ref): monochromatic */

@@ -89,6 +89,11 @@ def _load() -> ctypes.CDLL:
     lib.dtree_knn_noalloc.argtypes = [_P, _P, _I32, _P, _P, ctypes.POINTER(dtree_opts), _P]
     lib.dtree_kfn.argtypes = [_P, _P, _I32, _P, _P, ctypes.POINTER(dtree_opts), _P,
                               ctypes.POINTER(dtree_stats)]
+    lib.dtree_range_count.argtypes = [_P, _P, ctypes.c_double, ctypes.c_double, _P,
+                                      ctypes.POINTER(_I64), ctypes.POINTER(dtree_opts), _P,
+                                      ctypes.POINTER(dtree_stats)]
+    lib.dtree_range_fill.argtypes = [_P, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P,
+                                     ctypes.POINTER(dtree_opts), _P]
     lib.dtree_knn_batch.argtypes = [_I32, ctypes.POINTER(dtree_problem), ctypes.POINTER(dtree_opts),
                                     _P, ctypes.POINTER(dtree_stats)]
     lib.dtree_proposal_train.argtypes = [_P, _P, _I32, ctypes.POINTER(dtree_train_opts), _P,
@@ -369,6 +374,41 @@ def dtree_kfn(query: Optional[Tree], ref: Tree, k: int, out_idx: Optional[torch.
     if with_stats:
         return out_idx, out_dist, {f: int(getattr(st, f)) for f in STAT_FIELDS}
     return out_idx, out_dist
+
+
+def dtree_range(query: Optional[Tree], ref: Tree, d_lo: float, d_hi: float, stream=None,
+                with_stats: bool = False, precision: str = "fp32"):
+    """Exact range search: every reference point with d_lo <= distance <=
+    d_hi for every point of ``query`` (None = monochromatic).  Returns
+    (offsets int64 (n_q + 1), idx int64 (total), dist float32 (total)) on the
+    device: query row i's neighbours are idx[offsets[i]:offsets[i + 1]] (a
+    set, in the search's visit order), plus a dict of counters when
+    ``with_stats``."""
+    nq = ref.n if query is None else query.n
+    dev = torch.device("cuda", torch.cuda.current_device())
+    qh = None if query is None else query.handle
+    offsets = torch.empty(nq + 1, dtype=torch.int64, device=dev)
+    total = _I64(0)
+    o = _opts(precision=PRECISIONS[precision])
+    st = dtree_stats()
+    rc = _lib.dtree_range_count(qh, ref.handle, float(d_lo), float(d_hi),
+                                ctypes.c_void_p(offsets.data_ptr()), ctypes.byref(total),
+                                ctypes.byref(o), _stream(stream),
+                                ctypes.byref(st) if with_stats else None)
+    if rc != DTREE_OK:
+        raise DTreeError(rc, "dtree_range_count")
+    n = int(total.value)
+    idx = torch.empty(n, dtype=torch.int64, device=dev)
+    dist = torch.empty(n, dtype=torch.float32, device=dev)
+    if n > 0:
+        rc = _lib.dtree_range_fill(qh, ref.handle, float(d_lo), float(d_hi),
+                                   ctypes.c_void_p(offsets.data_ptr()), ctypes.c_void_p(idx.data_ptr()),
+                                   ctypes.c_void_p(dist.data_ptr()), ctypes.byref(o), _stream(stream))
+        if rc != DTREE_OK:
+            raise DTreeError(rc, "dtree_range_fill")
+    if with_stats:
+        return offsets, idx, dist, {f: int(getattr(st, f)) for f in STAT_FIELDS}
+    return offsets, idx, dist
 
 
 def dtree_knn_noalloc(query: Optional[Tree], ref: Tree, k: int, out_idx: torch.Tensor,
