@@ -56,8 +56,10 @@ def parse():
     p.add_argument("--cpu-queries", type=int, default=8192)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ref-queries", type=int, default=512)
-    p.add_argument("--op", choices=["knn", "kfn"], default="knn",
-                   help="knn: the headline; kfn: exact k-furthest neighbours on the same workload")
+    p.add_argument("--op", choices=["knn", "kfn", "range"], default="knn",
+                   help="knn: the headline; kfn: exact k-furthest neighbours and range: exact "
+                        "range search, on the same workload")
+    p.add_argument("--range", type=float, nargs=2, default=[0.0, 2.5], metavar=("D_LO", "D_HI"))
     return p.parse_args()
 
 
@@ -253,7 +255,7 @@ def job_rate(world, n_per_rank, ms_max):
 def main():
     args = parse()
     rank, world, local = dist_env()
-    if args.op == "kfn":
+    if args.op in ("kfn", "range"):
         run_kfn(args, rank, world, local)
         return
     if args.impl == "reference":
@@ -385,13 +387,28 @@ def main():
 
 METRIC_KFN = "exact k-furthest-neighbour queries/s (oracle-identical)"
 WORKLOAD_KFN = WORKLOAD.replace("exact kNN", "exact k-furthest neighbours")
+METRIC_RANGE = "exact range-search queries/s (oracle-identical)"
 
 
 def run_kfn(args, rank, world, local):
-    """One step = build the reference tree + build the query tree + dtree_kfn
-    (one warp per query: the single-tree depth-first search with the inverted
-    Score and BaseCase, float32 keys, float64 re-rank and fallback)."""
+    """--op kfn: one step = build the reference tree + build the query tree +
+    dtree_kfn (one warp per query: the single-tree depth-first search with the
+    inverted Score and BaseCase, float32 keys, float64 re-rank and fallback).
+    --op range: the same with dtree_range (count, scan, fill) over --range."""
     from oracle import kfn as okfn
+    from oracle import rangesearch as orange
+    is_range = args.op == "range"
+    d_lo, d_hi = args.range
+    metric = METRIC_RANGE if is_range else METRIC_KFN
+    workload = (WORKLOAD.replace("exact kNN", f"exact range search [{d_lo:g}, {d_hi:g}]")
+                .replace(", k=10", "") if is_range else WORKLOAD_KFN)
+
+    def oracle_call(ref, qry, k):
+        if is_range:
+            orange.range_brute(ref, qry, d_lo, d_hi)
+        else:
+            okfn.kfn_brute(ref, qry, k)
+
     if args.impl == "reference":
         if rank != 0:
             return
@@ -401,20 +418,20 @@ def run_kfn(args, rank, world, local):
         for step in range(args.warmup + args.steps):
             lo = (step * nq) % max(1, len(W.query) - nq)
             t0 = time.perf_counter()
-            okfn.kfn_brute(W.ref, W.query[lo:lo + nq], W.k)
+            oracle_call(W.ref, W.query[lo:lo + nq], W.k)
             if step >= args.warmup:
                 times.append(time.perf_counter() - t0)
         t = sum(times) / len(times)
         value = nq / t
         print(json.dumps({
-            "impl": "reference", "metric": METRIC_KFN, "value": value, "unit": UNIT,
+            "impl": "reference", "metric": metric, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_KFN, "step": f"{nq}-query sample per step, brute force"},
+            "config": {"workload": workload, "step": f"{nq}-query sample per step, brute force"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{nq} queries per step vs all {len(W.ref)} references, "
-                                       "float64 brute force (oracle.kfn.kfn_brute, numpy)"},
+                                       "float64 brute force (numpy, one thread)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }), flush=True)
         return
@@ -433,12 +450,18 @@ def run_kfn(args, rank, world, local):
     out_dist = torch.empty((nq, k), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    res = {}
+
     def step(ref, qry):
         tr = dtree.dtree_build(ref, args.leaf)
         tq = dtree.dtree_build(qry, args.leaf)
         try:
-            _, _, st = dtree.dtree_kfn(tq, tr, k, out_idx=out_idx, out_dist=out_dist,
-                                       with_stats=True)
+            if is_range:
+                res["off"], res["idx"], res["dist"], st = dtree.dtree_range(
+                    tq, tr, d_lo, d_hi, with_stats=True)
+            else:
+                _, _, st = dtree.dtree_kfn(tq, tr, k, out_idx=out_idx, out_dist=out_dist,
+                                           with_stats=True)
         finally:
             tr.free()
             tq.free()
@@ -477,12 +500,19 @@ def run_kfn(args, rank, world, local):
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
+    d2h = 0
     for _ in range(args.e2e_steps):
         ref_e.copy_(ref_h, non_blocking=True)
         q_e.copy_(q_h, non_blocking=True)
         step(ref_e, q_e)
-        idx_h.copy_(out_idx, non_blocking=True)
-        dist_h.copy_(out_dist, non_blocking=True)
+        if is_range:
+            outs = [res["off"].to("cpu", non_blocking=True), res["idx"].to("cpu", non_blocking=True),
+                    res["dist"].to("cpu", non_blocking=True)]
+            d2h = sum(int(t.numel() * t.element_size()) for t in outs)
+        else:
+            idx_h.copy_(out_idx, non_blocking=True)
+            dist_h.copy_(out_dist, non_blocking=True)
+            d2h = int(nq * k * (8 + 4))
     f1.record(stream)
     torch.cuda.synchronize()
     e2e_value = job_rate(world, nq, max_over_ranks(f0.elapsed_time(f1) / args.e2e_steps, world, "cuda"))
@@ -501,32 +531,39 @@ def run_kfn(args, rank, world, local):
     achieved = flops / (ns * 1e-9) / 1e12 if ns > 0 else 0.0
     s0 = stats[-1]
     line = {
-        "metric": METRIC_KFN, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_KFN, "precision": "fp32 keys, f64 re-rank", "leaf_size": args.leaf,
-                   "step": "build ref tree + build query tree + dtree_kfn",
+        "config": {"workload": workload, "precision": "fp32 keys, f64 decisions", "leaf_size": args.leaf,
+                   "step": "build ref tree + build query tree + "
+                           + ("dtree_range (count, scan, fill)" if is_range else "dtree_kfn"),
                    "l2": "inputs (320 MB) larger than the 129 MB L2; no flush",
                    "parallelism": f"{world} GPU(s), one query shard each, reference replicated"},
-        "roofline": {"bound": "alu", "kernel": "k_kfn (one warp per query, float32 keys)",
+        "roofline": {"bound": "alu",
+                     "kernel": ("k_range count launch" if is_range else "k_kfn")
+                     + " (one warp per query, float32 keys)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None, "traffic": None,
                      "peak_source": f"2 x 128 FP32 lanes x {sms} SMs x {sm_max:.0f} MHz",
                      "algorithmic_flops_per_step": flops, "point_pairs_per_step": pairs,
                      "kernel_ms": ns / 1e6},
-        "phases_ms": {"kfn": ns / 1e6, "build_and_rest": ms_max - ns / 1e6},
+        "phases_ms": {("range_count" if is_range else "kfn"): ns / 1e6,
+                      "build_and_rest": ms_max - ns / 1e6},
         "counters": {k2: s0[k2] for k2 in ("point_pairs", "leaf_pairs_evaluated",
-                                          "node_pairs_pruned", "fallback_queries")},
+                                          "node_pairs_pruned", "fallback_queries",
+                                          "rerank_candidates")},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(W.ref.nbytes + W.query.nbytes),
-                "d2h_bytes_per_step": int(nq * k * (8 + 4))},
+                "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clock_info,
     }
+    if is_range:
+        line["counters"]["results"] = int(res["off"][-1].item())
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nb = 16
         t0 = time.perf_counter()
-        okfn.kfn_brute(W.ref, W.query[:nb], k)
+        oracle_call(W.ref, W.query[:nb], k)
         dt_ = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": nb / dt_, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"float64 brute force (numpy, one thread) for the first {nb} "
