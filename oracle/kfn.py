@@ -1,7 +1,7 @@
 """Float64 reference of k-furthest-neighbour search -- TEST INFRASTRUCTURE ONLY.
 
-Only the tests and ``__graft_entry__.smoke()`` import this module; the CUDA
-library never calls it.
+Only the tests and ``bench.py``'s CPU legs (its ``cpu_baseline`` and
+reference arm) import this module; the CUDA library never calls it.
 
 Problem (Section 5, the paragraph on k-furthest neighbour search after
 Algorithm 4): for every query, the k reference points at the LARGEST

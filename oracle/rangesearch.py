@@ -1,6 +1,7 @@
 """Float64 reference of range search -- TEST INFRASTRUCTURE ONLY.
 
-Only the tests import this module; the CUDA library never calls it.
+Only the tests and ``bench.py``'s CPU legs (its ``cpu_baseline`` and
+reference arm) import this module; the CUDA library never calls it.
 
 Problem (Section 6, "Range Search"): given a range [delta1, delta2], for every
 query p_q all reference points p_r with delta1 <= ||p_q - p_r|| <= delta2
