@@ -11,7 +11,8 @@ of the paper it follows.  ``mlp.py`` holds the double-precision reference of
 the learned proposal's network, ``kfn.py`` the k-furthest-neighbour problem
 (its brute-force definition and the inverted dual-tree), and
 ``rangesearch.py`` range search (its definition and the dual-tree with the
-range Score).
+range Score), and ``emst.py`` the Euclidean minimum spanning tree (Kruskal
+and Prim under one total edge order).
 """
 from __future__ import annotations
 
