@@ -223,6 +223,28 @@ int dtree_range_fill(const dtree_t* query, const dtree_t* ref, double d_lo, doub
                      const int64_t* offsets, int64_t* out_idx, float* out_dist,
                      const dtree_opts* opts, void* stream);
 
+/*
+ * dtree_emst -- the Euclidean minimum spanning tree of a tree's points by
+ * Boruvka rounds (Section 7): each round, every component's shortest edge to
+ * a point outside it (a pruning search per point, float64 distances), then
+ * the components joined by those edges merge.  Edges compare by float64
+ * squared length, equal lengths by (lower index, higher index), so the tree
+ * is unique.
+ *   tree      the points (any dimension the library builds)
+ *   out_edges device, (n - 1) x 2 int64: (lower, higher) caller row indices
+ *   out_dist  device, n - 1 float32: edge lengths, rounded once from float64
+ *   opts      nullable; precision must be DTREE_PREC_FP32
+ *   stats     nullable; point_pairs (distances), leaf_pairs_evaluated,
+ *             kernel_launches, ns_basecase
+ * Edges come round by round, and within a round by component; the order is
+ * the same from call to call.  Status: DTREE_ERR_INVALID_ARG (null tree or
+ * outputs with n > 1, a tree on another device), DTREE_ERR_UNSUPPORTED
+ * (another precision, a tree deeper than 30 levels), or a CUDA error.  One
+ * point gives no edge.  Waits for the result.
+ */
+int dtree_emst(const dtree_t* tree, int64_t* out_edges, float* out_dist, const dtree_opts* opts,
+               void* stream, dtree_stats* stats);
+
 /* One problem of a batch: the arguments of one dtree_knn call. */
 typedef struct dtree_problem {
     const dtree_t* query;   /* NULL (or == ref): monochromatic */

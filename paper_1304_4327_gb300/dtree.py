@@ -94,6 +94,7 @@ def _load() -> ctypes.CDLL:
                                       ctypes.POINTER(dtree_stats)]
     lib.dtree_range_fill.argtypes = [_P, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P,
                                      ctypes.POINTER(dtree_opts), _P]
+    lib.dtree_emst.argtypes = [_P, _P, _P, ctypes.POINTER(dtree_opts), _P, ctypes.POINTER(dtree_stats)]
     lib.dtree_knn_batch.argtypes = [_I32, ctypes.POINTER(dtree_problem), ctypes.POINTER(dtree_opts),
                                     _P, ctypes.POINTER(dtree_stats)]
     lib.dtree_proposal_train.argtypes = [_P, _P, _I32, ctypes.POINTER(dtree_train_opts), _P,
@@ -409,6 +410,28 @@ def dtree_range(query: Optional[Tree], ref: Tree, d_lo: float, d_hi: float, stre
     if with_stats:
         return offsets, idx, dist, {f: int(getattr(st, f)) for f in STAT_FIELDS}
     return offsets, idx, dist
+
+
+def dtree_emst(tree: Tree, stream=None, with_stats: bool = False, precision: str = "fp32"):
+    """The Euclidean minimum spanning tree of the tree's points (edges of equal
+    length ordered by their endpoints' indices, so it is unique): (edges int64
+    (n - 1, 2) as (lower, higher) caller row indices, dist float32 (n - 1)) on
+    the device, in the order the rounds found them, plus a dict of counters
+    when ``with_stats``."""
+    n = tree.n
+    dev = torch.device("cuda", torch.cuda.current_device())
+    edges = torch.empty((max(n - 1, 0), 2), dtype=torch.int64, device=dev)
+    dist = torch.empty(max(n - 1, 0), dtype=torch.float32, device=dev)
+    o = _opts(precision=PRECISIONS[precision])
+    st = dtree_stats()
+    rc = _lib.dtree_emst(tree.handle, ctypes.c_void_p(edges.data_ptr()) if edges.numel() else None,
+                         ctypes.c_void_p(dist.data_ptr()) if dist.numel() else None,
+                         ctypes.byref(o), _stream(stream), ctypes.byref(st) if with_stats else None)
+    if rc != DTREE_OK:
+        raise DTreeError(rc, "dtree_emst")
+    if with_stats:
+        return edges, dist, {f: int(getattr(st, f)) for f in STAT_FIELDS}
+    return edges, dist
 
 
 def dtree_knn_noalloc(query: Optional[Tree], ref: Tree, k: int, out_idx: torch.Tensor,
