@@ -56,7 +56,7 @@ def parse():
     p.add_argument("--cpu-queries", type=int, default=8192)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ref-queries", type=int, default=512)
-    p.add_argument("--op", choices=["knn", "kfn", "range"], default="knn",
+    p.add_argument("--op", choices=["knn", "kfn", "range", "emst"], default="knn",
                    help="knn: the headline; kfn: exact k-furthest neighbours and range: exact "
                         "range search, on the same workload")
     p.add_argument("--range", type=float, nargs=2, default=[0.0, 2.5], metavar=("D_LO", "D_HI"))
@@ -257,6 +257,9 @@ def main():
     rank, world, local = dist_env()
     if args.op in ("kfn", "range"):
         run_kfn(args, rank, world, local)
+        return
+    if args.op == "emst":
+        run_emst(args, rank, world, local)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -568,6 +571,130 @@ def run_kfn(args, rank, world, local):
         line["cpu_baseline"] = {"value": nb / dt_, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"float64 brute force (numpy, one thread) for the first {nb} "
                                           f"queries against all {len(W.ref)} references; {dt_:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# the Euclidean minimum spanning tree (--op emst)
+# ---------------------------------------------------------------------------
+
+METRIC_EMST = "exact Euclidean MST points/s (oracle-identical edges)"
+
+
+def run_emst(args, rank, world, local):
+    """One step = build the tree + dtree_emst (Boruvka rounds) on --n-ref
+    uniform points in d = 3 (the mixture of the kNN workload at d = 16 takes
+    seconds per round; see the design notes).  One problem per GPU: under
+    torchrun every rank solves its own point set."""
+    from oracle import emst as oemst
+    n = args.n_ref if args.n_ref != 4_000_000 else 1_000_000
+    P = inputs.uniform(n, 3, 7 + rank)
+    workload = f"emst: uniform U[0,1]^3, N={n:,}, leaf {args.leaf}"
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        m = 2000
+        times = []
+        for step in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            oemst.emst_kruskal(P[:m])
+            if step >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        t = sum(times) / len(times)
+        print(json.dumps({"impl": "reference", "metric": METRIC_EMST, "value": m / t, "unit": "points/s",
+                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": workload, "step": f"Kruskal on the first {m} points"},
+                          "cpu_baseline": {"value": m / t, "unit": "points/s", "cores": 1, "kind": "oracle",
+                                           "sample": f"float64 Kruskal over all pairs of the first {m} points"},
+                          "e2e": {"value": m / t, "unit": "points/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1304_4327_gb300 import dtree
+    p_d = torch.from_numpy(P).cuda()
+    stream = torch.cuda.current_stream()
+    res = {}
+
+    def step(pts):
+        t = dtree.dtree_build(pts, args.leaf)
+        try:
+            res["e"], res["d"], st = dtree.dtree_emst(t, with_stats=True)
+        finally:
+            t.free()
+        return st
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(p_d)
+    props = torch.cuda.get_device_properties(local)
+    uuid = getattr(props, "uuid", None)
+    clocks = ClockSampler(f"GPU-{uuid}" if uuid else None)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = dtree.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = [step(p_d) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clock_info = clocks.stop()
+    launches = dtree.launch_count() - launches0
+    ms_max = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
+    value = job_rate(world, n, ms_max)
+    p_h = torch.from_numpy(P).pin_memory()
+    p_e = torch.empty_like(p_d)
+    barrier()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.e2e_steps):
+        p_e.copy_(p_h, non_blocking=True)
+        step(p_e)
+        res["e"].to("cpu", non_blocking=True)
+        res["d"].to("cpu", non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value = job_rate(world, n, max_over_ranks(f0.elapsed_time(f1) / args.e2e_steps, world, "cuda"))
+    ns = sum(s["ns_basecase"] for s in stats) / len(stats)
+    pairs = sum(s["point_pairs"] for s in stats) / len(stats)
+    line = {
+        "metric": METRIC_EMST, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload, "step": "build tree + dtree_emst (Boruvka rounds)",
+                   "l2": "inputs (12 MB) fit L2; every step rebuilds the tree",
+                   "parallelism": f"{world} GPU(s), one problem each"},
+        "roofline": {"bound": "latency", "kernel": "k_emst_nn (one warp per point, float64 distances)",
+                     "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
+                     "note": "a chain of dependent box loads and shuffles per point; see profiles"},
+        "phases_ms": {"emst": ns / 1e6, "build_and_rest": ms_max - ns / 1e6},
+        "counters": {"point_pairs": pairs, "leaf_pairs_evaluated": stats[-1]["leaf_pairs_evaluated"]},
+        "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": int(P.nbytes),
+                "d2h_bytes_per_step": int((n - 1) * (16 + 4))},
+        "gpu_launches": int(launches),
+        "clocks": clock_info,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        m = 2000
+        t0 = time.perf_counter()
+        oemst.emst_kruskal(P[:m])
+        dt_ = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": m / dt_, "unit": "points/s", "cores": 1, "kind": "oracle",
+                                "sample": f"float64 Kruskal over all pairs of the first {m} points; {dt_:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
