@@ -678,9 +678,10 @@ def run_emst(args, rank, world, local):
         "config": {"workload": workload, "step": "build tree + dtree_emst (Boruvka rounds)",
                    "l2": "inputs (12 MB) fit L2; every step rebuilds the tree",
                    "parallelism": f"{world} GPU(s), one problem each"},
-        "roofline": {"bound": "latency", "kernel": "k_emst_nn (one warp per point, float64 distances)",
+        "roofline": {"bound": "fp64", "kernel": "k_emst_nn (one warp per point, float64 distances)",
                      "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
-                     "note": "a chain of dependent box loads and shuffles per point; see profiles"},
+                     "note": "the float64 pipe is the limit (about 80% busy in the ncu capture, "
+                             "profiles/k_emst_nn_uniform3.md); no algorithmic-flop count is claimed"},
         "phases_ms": {"emst": ns / 1e6, "build_and_rest": ms_max - ns / 1e6},
         "counters": {"point_pairs": pairs, "leaf_pairs_evaluated": stats[-1]["leaf_pairs_evaluated"]},
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": int(P.nbytes),
