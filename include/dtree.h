@@ -7,7 +7,10 @@
  * with the kd-tree bounds of Section 3), a pruning dual-tree traversal (the
  * pruning dual-tree traversal definition of Section 4), the kNN BaseCase
  * (Algorithm 2) and the kNN Score (Algorithm 3) with the bound B(N_q) of
- * Section 5.
+ * Section 5.  The same trees serve three more instances the paper derives:
+ * k-furthest neighbours (dtree_kfn, the extension after Algorithm 4), range
+ * search (dtree_range_count / dtree_range_fill, Section 6) and the Euclidean
+ * minimum spanning tree by Boruvka rounds (dtree_emst, Section 7).
  *
  * Conventions for every entry point:
  *   - Point arrays are row-major n x d float32.  Pointers marked "device" must
