@@ -44,6 +44,16 @@ def test_argument_checks_need_no_gpu(lib):
     assert lib.dtree_build(ctypes.c_void_p(16), 0, 3, None, None, ctypes.byref(out)) == -1
     lib.dtree_knn.argtypes = [ctypes.c_void_p] * 2 + [ctypes.c_int32] + [ctypes.c_void_p] * 5
     assert lib.dtree_knn(None, None, 3, None, None, None, None, None) == -1
+    # the other instances reject a missing tree before any CUDA call too
+    lib.dtree_kfn.argtypes = [ctypes.c_void_p] * 2 + [ctypes.c_int32] + [ctypes.c_void_p] * 5
+    assert lib.dtree_kfn(None, None, 3, None, None, None, None, None) == -1
+    P, D = ctypes.c_void_p, ctypes.c_double
+    lib.dtree_range_count.argtypes = [P, P, D, D, P, P, P, P, P]
+    assert lib.dtree_range_count(None, None, 0.0, 1.0, None, None, None, None, None) == -1
+    lib.dtree_range_fill.argtypes = [P, P, D, D, P, P, P, P, P]
+    assert lib.dtree_range_fill(None, None, 0.0, 1.0, None, None, None, None, None) == -1
+    lib.dtree_emst.argtypes = [P] * 6
+    assert lib.dtree_emst(None, None, None, None, None, None) == -1
     lib.dtree_size.restype = ctypes.c_int64
     lib.dtree_size.argtypes = [ctypes.c_void_p]
     assert lib.dtree_size(None) == -1
