@@ -357,7 +357,9 @@ static void refresh_bounds(kctx* c, int32_t n) {
     c->B1[n] = b1;
     c->A[n] = a;
     c->Blit[n] = fmin(b1, a + 2.0 * t->lambda[n]);      /* terms 1 and 2, leaf (R5) */
-    for (int32_t p = t->parent[n]; p >= 0; p = t->parent[p]) {
+    /* the walk ends at this context's own subtree root: a leaf that is the
+     * root itself has no ancestor of its own to refresh */
+    for (int32_t p = (n == c->stop) ? -1 : t->parent[n]; p >= 0; p = t->parent[p]) {
         int32_t l = t->left[p], r = t->right[p];
         c->B1[p] = fmax(c->B1[l], c->B1[r]);
         c->A[p] = fmin(c->A[l], c->A[r]);
