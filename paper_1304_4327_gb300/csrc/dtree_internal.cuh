@@ -37,6 +37,9 @@ struct dtree {
     int64_t cap_hint = 0;
     // learned proposal attached to this reference tree (not owned), or null
     const dtree_model* proposal = nullptr;
+    // tensor-core operand rows of the points (TF32, split BF16), made by the
+    // first search that needs them and owned by the handle
+    void* tc_ops[2] = {nullptr, nullptr};
 };
 
 namespace dt {

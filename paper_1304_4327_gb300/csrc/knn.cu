@@ -555,15 +555,15 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int cap
     const int64_t launches0 = g_launches.load();
     const int fmt = prec == DTREE_PREC_BF16 ? 1 : prec == DTREE_PREC_TF32 ? 2 : 0;
     // list length: k plus room for the candidates inside the error band
-    // (TF32 and split BF16 bands ~1% of d^2 at d=16, single BF16 ~5%, used
-    // beyond 32 dimensions); buckets 4, 8, 16, 24, 32
+    // (the TF32 and split-BF16 bands hold a few per cent more points than
+    // k); buckets 4, 8, 16, 24, 32, 48, 64
     int kmax = 0;
     for (int i = 0; i < np; ++i) kmax = std::max(kmax, hp[i].k);
-    const int kc_need = fmt == 1 ? (DP <= 32 ? kmax + 14 : 2 * kmax + 12) : fmt == 2 ? kmax + 14 : kmax + 1;
-    // float32 lists hold up to 64 entries (k <= 63), tensor-core lists up to 32
-    // (k <= 31; a band wider than the list sends its queries to the fallback)
-    if (kmax + 1 > (fmt ? 32 : 64)) return DTREE_ERR_UNSUPPORTED;
-    const int KC = std::min(kc_bucket(kc_need), fmt ? 32 : 64);
+    const int kc_need = fmt ? kmax + 14 : kmax + 1;
+    // lists hold up to 64 entries (k <= 63; a band wider than the list sends
+    // its queries to the fallback)
+    if (kmax + 1 > 64) return DTREE_ERR_UNSUPPORTED;
+    const int KC = std::min(kc_bucket(kc_need), 64);
 
     // the problems' layout in the batch-wide arrays
     ProbDev one[1];
@@ -607,6 +607,7 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int cap
         P.rbeg = tr->nbeg;
         P.rcnt = tr->ncnt;
         P.rbox = tr->box;
+        P.rn = m;
         P.out_idx = hp[i].out_idx;
         P.out_dist = hp[i].out_dist;
         P.k = hp[i].k;
@@ -626,6 +627,35 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int cap
     Pool P;
     P.s = s;
     P.arena = arena;
+    if (fmt) {
+        // the reference points as tensor-core operand rows (made once per
+        // tree and format, or carved from the fixed range for this call)
+        for (int i = 0; i < np; ++i) {
+            const dtree_t* tr = hp[i].tr;
+            const int64_t maxleaf = (tr->n + tr->nleaves - 1) / tr->nleaves;
+            const int ls = (int)((maxleaf + 7) / 8 * 8);
+            void*& cache = const_cast<dtree_t*>(tr)->tc_ops[fmt == 2 ? 0 : 1];
+            void* ops = cache;
+            if (!ops) {
+                const size_t bytes = (size_t)tr->nleaves * ls * tc_ops_row_bytes<DP>(fmt);
+                if (arena) {
+                    unsigned char* p = nullptr;
+                    DT_TRY(P.get(&p, bytes));
+                    ops = p;
+                } else {
+                    g_allocs.fetch_add(1, std::memory_order_relaxed);
+                    if (cudaMalloc(&ops, bytes) != cudaSuccess) {
+                        cudaGetLastError();
+                        return DTREE_ERR_OOM;
+                    }
+                    cache = ops;
+                }
+                DT_TRY(launch_tc_ops<DP>(tr, fmt, ls, ops, s));
+            }
+            pd[i].rops = ops;
+            pd[i].rls8 = ls / 8;
+        }
+    }
     ProbDev* probs;
     int32_t *blk_prob, *node_prob, *sl0, *sn, *cand_i, *csr_leaf = nullptr;
     int2 *items, *roots;
@@ -852,7 +882,7 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int cap
     a.Bn = Bn;
     a.work_ctr = ctr + 1;
     if (fmt)
-        DT_TRY(launch_tile_tc<DP>(a, fmt, KC, MODE_MAIN, NI, derr, spin, s));
+        DT_TRY(launch_tile_tc<DP>(a, fmt, KC, NI, derr, spin, s));
     else
         DT_TRY(launch_tile_cc<DP>(a, KC, MODE_MAIN, NI, s));
     tm.mark();  // 3

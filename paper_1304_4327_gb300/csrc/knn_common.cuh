@@ -41,13 +41,16 @@ struct ProbDev {
     const int32_t* qbeg;
     const int32_t* qcnt;
     const float* qlam;
-    const float* qbox;  // nodes x 2 x DP (the block's box gives the tensor-core centring point)
+    const float* qbox;  // nodes x 2 x DP
     // reference tree
     const float* rpts;
     const int32_t* ridx;
     const int32_t* rbeg;
     const int32_t* rcnt;
-    const float* rbox;
+    const float* rbox;  // nodes x 2 x DP; the root box's centre is the tensor-core centring point
+    const void* rops;   // tensor-core operand rows of the reference points (or null)
+    int64_t rls8;       // 8-row groups per leaf in rops
+    int64_t rn;         // reference points (leaf ranges follow from it and hr)
     // outputs, rows in the caller's query order
     int64_t* out_idx;
     float* out_dist;
@@ -107,9 +110,17 @@ int launch_query_cap(const TileArgs& a, int kc, int budget, float* qcap, cudaStr
 template <int DP>
 int launch_query_fb(const TileArgs& a, int kc, int nfbq, bool exact, cudaStream_t s);
 
+// The tensor-core BaseCase pass (main mode): fmt 1 = BF16 (split), 2 = TF32.
 template <int DP>
-int launch_tile_tc(const TileArgs& a, int fmt, int kc, int mode, int items, int* err, int spin,
+int launch_tile_tc(const TileArgs& a, int fmt, int kc, int items, int* err, int spin,
                    cudaStream_t s);
+
+// Bytes per operand row, and the fill of a reference tree's operand array
+// (nleaves x ls rows, ls a multiple of 8) for the tensor-core pass.
+template <int DP>
+size_t tc_ops_row_bytes(int fmt);
+template <int DP>
+int launch_tc_ops(const dtree_t* t, int fmt, int ls, void* out, cudaStream_t s);
 
 // A block's seed: up to `slots` disjoint subtrees of the reference tree,
 // slot s covering leaves [leaf0[s], leaf0[s] + nleaf[s]).

@@ -2,5 +2,7 @@
 #include "knn_tc.cuh"
 
 namespace dt {
-template int launch_tile_tc<4>(const TileArgs&, int, int, int, int, int*, int, cudaStream_t);
+template int launch_tile_tc<4>(const TileArgs&, int, int, int, int*, int, cudaStream_t);
+template size_t tc_ops_row_bytes<4>(int);
+template int launch_tc_ops<4>(const dtree_t*, int, int, void*, cudaStream_t);
 }  // namespace dt

@@ -7,6 +7,7 @@
 
 namespace dt {
 unsigned long long* g_tc_timers = nullptr;
+int g_tc_stall = 0;
 namespace {
 
 template <int FMT, int KP>
@@ -142,5 +143,10 @@ extern "C" int dtree_debug_mma(const float* A, const float* B, int32_t K, int32_
 
 extern "C" int dtree_debug_tc_timers(unsigned long long* counters) {
     dt::g_tc_timers = counters;
+    return DTREE_OK;
+}
+
+extern "C" int dtree_debug_tc_stall(int32_t on) {
+    dt::g_tc_stall = on ? 1 : 0;
     return DTREE_OK;
 }

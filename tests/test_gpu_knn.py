@@ -242,16 +242,22 @@ def test_powerlaw64_scaled(dt):
 
 
 def test_powerlaw64_k50_scaled(dt):
-    # the power-law workload's own k (lists of 64 on the CUDA cores)
+    # the power-law workload's own k (lists of 64), on the CUDA cores and the
+    # tensor cores
     W = inputs.powerlaw64(n_ref=40_000, n_query=3_000)
     assert W.k == 50
     check(dt, W.ref, W.query, W.k, W.leaf_size)
     check(dt, W.ref[:20_000], None, W.k, W.leaf_size)
-    # tensor-core lists hold at most 32 entries
     for prec in ("bf16", "tf32"):
-        with pytest.raises(dt.DTreeError) as e:
-            run(dt, W.ref, W.query, W.k, W.leaf_size, precision=prec)
-        assert e.value.status == -7
+        check(dt, W.ref, W.query, W.k, W.leaf_size, precision=prec)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
+def test_k_above_63_is_unsupported(dt, prec):
+    R = inputs.gaussian(3000, 8, 11)
+    with pytest.raises(dt.DTreeError) as e:
+        run(dt, R, None, 64, 16, precision=prec)
+    assert e.value.status == -7          # DTREE_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("k", [32, 47, 48, 63])

@@ -49,11 +49,6 @@ def test_mma_tile_layout(dt, fmt, K):
 def test_tc_parity_dims(dt, prec, d, mono):
     R = inputs.gaussian(4001, d, 500 + d)
     Q = None if mono else inputs.uniform(1203, d, 600 + d) * 2 - 1
-    if prec == "tf32" and d > 32:
-        with pytest.raises(dt.DTreeError) as e:
-            run(dt, R, Q, 5, 16, precision=prec)
-        assert e.value.status == -7          # DTREE_ERR_UNSUPPORTED
-        return
     for k in (1, 5, 10):
         idx, dist = run(dt, R, Q, k, 16, precision=prec)
         ti, td = truth(R, Q, k)
@@ -84,8 +79,8 @@ def test_tc_duplicates(dt, prec):
 
 @pytest.mark.parametrize("prec", ["bf16", "tf32"])
 def test_tc_offset_cloud(dt, prec):
-    # a cloud far from the origin: centring on the query block keeps the
-    # rounded coordinates small
+    # a cloud far from the origin: centring on the reference root box keeps
+    # the rounded coordinates small
     R = inputs.gaussian(20000, 16, 31) + 1000.0
     Q = inputs.gaussian(3000, 16, 32) + 1000.0
     idx, dist = run(dt, R.astype(np.float32), Q.astype(np.float32), 10, 32, precision=prec)
@@ -97,7 +92,7 @@ def test_tc_offset_cloud(dt, prec):
 def test_tc_k_values(dt, prec):
     R = inputs.gaussian(6000, 32, 41)
     Q = inputs.gaussian(1500, 32, 42)
-    for k in (1, 2, 7, 15, 31):
+    for k in (1, 2, 7, 15, 31, 34, 47, 50, 63):
         idx, dist = run(dt, R, Q, k, 32, precision=prec)
         ti, td = truth(R, Q, k)
         compare(idx, dist, ti, td, k)
@@ -112,3 +107,49 @@ def test_tc_gmm16_full_size_sampled(dt):
     ti, td = truth(W.ref, W.query, W.k, sample)
     r = compare(idx[sample], dist[sample], ti, td, W.k)
     assert r["exact"] + r["exempt"] == 256
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("d", [5, 16, 64])
+@pytest.mark.parametrize("leaf", [1, 5, 20, 37, 300])
+def test_tc_leaf_sizes(dt, prec, d, leaf):
+    # leaves of every size pad to whole 8-row groups of the operand rows; a
+    # leaf wider than a tile (300 > 256 or 128 points) is split across tiles
+    R = inputs.gaussian(7001, d, 700 + d + leaf)
+    Q = inputs.gaussian(1501, d, 800 + d + leaf)
+    for q, k in ((Q, 10), (None, 3)):
+        idx, dist = run(dt, R, q, k, leaf, precision=prec)
+        ti, td = truth(R, q, k)
+        compare(idx, dist, ti, td, k)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_tc_powerlaw64_k50(dt, prec):
+    """The combined workload's shape (d = 64, k = 50) at 60k x 6k: every query."""
+    W = inputs.powerlaw64(n_ref=60_000, n_query=6_000)
+    assert W.k == 50
+    idx, dist, st = run(dt, W.ref, W.query, W.k, W.leaf_size, stats=True, precision=prec)
+    ti, td = truth(W.ref, W.query, W.k)
+    r = compare(idx, dist, ti, td, W.k)
+    assert r["exact"] + r["exempt"] == 6_000
+    # lists of 64 hold the band: overflows are rare (they are recomputed
+    # exactly, so this bounds cost, not correctness)
+    assert st["fallback_queries"] <= 60, st["fallback_queries"]
+    # monochromatic, with the self-match excluded
+    idx, dist = run(dt, W.ref[:20_000], None, W.k, W.leaf_size, precision=prec)
+    ti, td = truth(W.ref[:20_000], None, W.k)
+    compare(idx, dist, ti, td, W.k)
+
+
+@pytest.mark.skipif(os.environ.get("DTREE_SKIP_FULL") == "1", reason="full-size run disabled")
+def test_tc_powerlaw64_full_size_sampled(dt):
+    """2M x 2M, d = 64, k = 50 in split BF16: 256 sampled queries against brute
+    force, and fewer than 0.1% of the queries recomputed."""
+    W = inputs.powerlaw64()
+    idx, dist, st = run(dt, W.ref, W.query, W.k, W.leaf_size, stats=True, precision="bf16")
+    rng = np.random.default_rng(7)
+    sample = np.sort(rng.choice(len(W.query), 256, replace=False))
+    ti, td = truth(W.ref, W.query, W.k, sample)
+    r = compare(idx[sample], dist[sample], ti, td, W.k)
+    assert r["exact"] + r["exempt"] == 256
+    assert st["fallback_queries"] < len(W.query) // 1000, st["fallback_queries"]
