@@ -47,8 +47,10 @@ typedef enum dtree_status {
     DTREE_ERR_NOT_TRAINED = -6,  /* a learned proposal was requested without a model */
     DTREE_ERR_UNSUPPORTED = -7,  /* valid request this build/device cannot serve
                                     (e.g. tensor-core precision on a non-sm_103 device) */
-    DTREE_ERR_TOO_LARGE = -8     /* the problem exceeds the fixed scratch of
+    DTREE_ERR_TOO_LARGE = -8,    /* the problem exceeds the fixed scratch of
                                     dtree_knn_noalloc (see its limits) */
+    DTREE_ERR_IO = -9            /* a model file could not be written, read, or is not a
+                                    well-formed model file */
 } dtree_status;
 
 /* Distance arithmetic of the BaseCase tiles.  Whatever the choice, results
@@ -57,12 +59,11 @@ typedef enum dtree_status {
  * float64 (see dtree_knn). */
 typedef enum dtree_precision {
     DTREE_PREC_FP32 = 0,   /* CUDA-core float32 differences and squares */
-    DTREE_PREC_TF32 = 1,   /* tensor cores (tcgen05), TF32 inputs, FP32 accumulate
-                              (d <= 32; wider points return DTREE_ERR_UNSUPPORTED) */
-    DTREE_PREC_BF16 = 2    /* tensor cores (tcgen05), BF16 inputs, FP32 accumulate; for
-                              d <= 32 each centred coordinate is carried as a hi + lo pair
-                              of BF16 values (three BF16 products per term, operand error
-                              about 2^-16), beyond that as one BF16 value (2^-8) */
+    DTREE_PREC_TF32 = 1,   /* tensor cores (tcgen05), TF32 inputs, FP32 accumulate */
+    DTREE_PREC_BF16 = 2    /* tensor cores (tcgen05), BF16 inputs, FP32 accumulate: each
+                              centred coordinate is carried as a hi + lo pair of BF16
+                              values (three BF16 products per term, operand error about
+                              2^-16) */
 } dtree_precision;
 
 /* Options; zero-initialise and set what you need (0 = default). */
@@ -144,7 +145,8 @@ int dtree_build(const float* pts, int64_t n, int32_t d, const dtree_opts* opts, 
  *             footnote to Algorithm 2; exclusion is by index, so duplicates at
  *             distance 0 are valid neighbours).
  *   ref       tree of the references (m points).
- *   k         0 < k < m (bichromatic), 0 < k <= m - 1 (monochromatic).
+ *   k         0 < k < m (bichromatic), 0 < k <= m - 1 (monochromatic), and
+ *             k <= 63 (DTREE_ERR_UNSUPPORTED beyond).
  *   out_idx   device, n_q x k int64, row i = the query's row in the array it
  *             was built from; entries are row indices of the reference array,
  *             ascending by (distance, index) -- ties go to the lower index.
@@ -158,7 +160,11 @@ int dtree_build(const float* pts, int64_t n, int32_t d, const dtree_opts* opts, 
  * The call enqueues its kernels on `stream`, blocks the calling thread until
  * they finish (it reads device-side sizes between phases) and returns the
  * device-side status, so the outputs are ready on return.  Scratch memory
- * comes from the device's stream-ordered pool.
+ * comes from the device's stream-ordered pool.  With a tensor-core
+ * precision, the first search against a reference tree also converts its
+ * points once into the MMA's operand rows (centred on the root box's centre,
+ * rows x (32 to 288) bytes by dimension), which the tree keeps until
+ * dtree_free.
  */
 int dtree_knn(const dtree_t* query, const dtree_t* ref, int32_t k, int64_t* out_idx,
               float* out_dist, const dtree_opts* opts, void* stream, dtree_stats* stats);
@@ -359,6 +365,24 @@ typedef struct dtree_train_opts {
 int dtree_proposal_train(const dtree_t* ref, const dtree_t* train, int32_t k,
                          const dtree_train_opts* opts, void* stream, dtree_model** out);
 void dtree_model_free(dtree_model* model);
+
+/*
+ * dtree_model_save / dtree_model_load -- keep a trained proposal across
+ * processes (no counterpart in the paper).  The file (host path) holds the
+ * network's shape, the input standardisation, the FP32 weights and a
+ * fingerprint of the reference tree the model was trained for (its size,
+ * dimension, height and the bounding boxes of its cells), closed by a
+ * checksum.  Loading checks the file before it touches the device, then
+ * compares the fingerprint with `ref` (a tree built from the same points with
+ * the same leaf size matches) and returns a new library-owned model
+ * (dtree_model_free) whose searches propose exactly the cells the saved one
+ * did.  Status: DTREE_ERR_INVALID_ARG (null arguments, or a model for another
+ * tree: dimension, depth or fingerprint differ), DTREE_ERR_IO (the file cannot
+ * be written or read, is truncated, or fails the format or checksum checks),
+ * DTREE_ERR_OOM, or a CUDA error.  Both wait for their copies on `stream`.
+ */
+int dtree_model_save(const dtree_model* model, const char* path, void* stream);
+int dtree_model_load(const char* path, const dtree_t* ref, void* stream, dtree_model** out);
 /* Number of cells (output classes) of a model; -1 for NULL. */
 int dtree_model_classes(const dtree_model* model);
 /*
@@ -406,6 +430,11 @@ int64_t dtree_leaf_count(const dtree_t* tree);
 int dtree_export(const dtree_t* tree, int32_t* perm, float* box, float* lambda, int32_t* begin,
                  int32_t* count, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Diagnostics.  No counterpart in the paper: hooks for the tests and for
+ * profiling the hardware path.  They do not change any result.
+ * ------------------------------------------------------------------------- */
+
 /*
  * dtree_debug_mma -- diagnostic: one 128 x 128 tensor-core tile through the
  * operand layout, descriptors and TMEM read-out the BaseCase tiles use.
@@ -430,6 +459,17 @@ int dtree_debug_mma(const float* A, const float* B, int32_t K, int32_t precision
  * performance probe.)
  */
 int dtree_debug_tc_timers(unsigned long long* counters);
+
+/*
+ * dtree_debug_tc_stall -- diagnostic of the bounded waits: while `on` is
+ * non-zero, the tensor-core BaseCase pass makes every block's planner wait,
+ * before it ends the block, on a barrier that nothing completes.  That wait
+ * gives up after opts->spin_budget polls, the pass abandons its work items,
+ * lets its own copies and MMAs finish, releases its tensor memory, and the
+ * call returns DTREE_ERR_TIMEOUT with the context still usable (its outputs
+ * are not valid).  Process-wide; not thread-safe.
+ */
+int dtree_debug_tc_stall(int32_t on);
 
 /* Static description of a status code. */
 const char* dtree_error_string(int status);

@@ -44,6 +44,8 @@ void dtree_free(dtree_t* t) {
     cudaFree(t->lam);
     cudaFree(t->nbeg);
     cudaFree(t->ncnt);
+    cudaFree(t->tc_ops[0]);
+    cudaFree(t->tc_ops[1]);
     delete t;
 }
 
@@ -67,6 +69,7 @@ const char* dtree_error_string(int status) {
         case DTREE_ERR_TIMEOUT: return "device-side wait timed out";
         case DTREE_ERR_NOT_TRAINED: return "learned proposal requested without a trained model";
         case DTREE_ERR_UNSUPPORTED: return "unsupported on this build or device";
+        case DTREE_ERR_IO: return "model file cannot be written or read, or is malformed";
         default: return "unknown status";
     }
 }

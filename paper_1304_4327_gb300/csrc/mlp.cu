@@ -32,6 +32,7 @@ struct dtree_model {
     __half* wh[3] = {};    // FP16 copies of W1, W2, W3 for the GEMMs
     int64_t t = 0;         // Adam steps taken
     int device = 0;
+    uint64_t tree_hash = 0;  // fingerprint of the reference tree's cells (tree_fingerprint)
     int64_t size(int i) const {
         switch (i) {
             case 0: return (int64_t)H * dpad;
@@ -609,6 +610,35 @@ int proposal_cells(const dtree_model* md, const float* pts, int64_t n, int M, in
 
 int model_level(const dtree_model* md) { return md->level; }
 
+// Fingerprint of the reference tree a model's cells refer to: FNV-1a over
+// its size, dimension, height, the cell level and the bounding boxes of the
+// cells (the subtrees at that level).  A model only makes sense for a tree
+// with the same cells; trees built from the same points with the same leaf
+// size agree.
+int tree_fingerprint(const dtree_t* t, int level, uint64_t* out, cudaStream_t s) {
+    const int64_t cells = (int64_t)1 << level, node0 = cells - 1;
+    std::vector<float> box((size_t)(cells * 2 * t->dp));
+    DT_CHECK(cudaMemcpyAsync(box.data(), t->box + node0 * 2 * t->dp, box.size() * 4,
+                             cudaMemcpyDeviceToHost, s));
+    DT_CHECK(cudaStreamSynchronize(s));
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; ++i) {
+            h ^= b[i];
+            h *= 1099511628211ull;
+        }
+    };
+    const int64_t head[4] = {t->n, t->d, t->height, level};
+    mix(head, sizeof(head));
+    for (int64_t c = 0; c < cells; ++c) {
+        mix(box.data() + c * 2 * t->dp, (size_t)t->d * 4);           // lo
+        mix(box.data() + c * 2 * t->dp + t->dp, (size_t)t->d * 4);   // hi
+    }
+    *out = h;
+    return DTREE_OK;
+}
+
 int box_centres(const dtree_t* t, int64_t node0, int64_t count, float* out, cudaStream_t s) {
     if (count <= 0) return DTREE_OK;
     DT_LAUNCH(k_centres, (int)((count * t->d + 255) / 256), 256, 0, s, t->box, t->dp, t->d, node0,
@@ -692,6 +722,7 @@ int dtree_proposal_train(const dtree_t* ref, const dtree_t* train, int32_t k,
     }
     rc = dt::model_init(md, o && o->seed ? (uint64_t)o->seed : 1304432701ull, s);
     if (rc != DTREE_OK) return fail(rc);
+    if ((rc = dt::tree_fingerprint(ref, md->level, &md->tree_hash, s)) != DTREE_OK) return fail(rc);
 
     // the method's own answers for the training queries
     DevBuf<int64_t> nbr;
@@ -767,6 +798,131 @@ int dtree_proposal_train(const dtree_t* ref, const dtree_t* train, int32_t k,
 }
 
 void dtree_model_free(dtree_model* m) { dt::model_release(m); }
+
+// File layout (little-endian): the 8 magic bytes "DTRMODL1"; int32 d, dpad,
+// H, C, level; uint64 the tree fingerprint; int64 Adam steps; float32
+// mean[d], scale[d]; the six float32 parameter arrays W1, b1, W2, b2, W3, b3;
+// uint64 FNV-1a of every byte before it.
+static const char kModelMagic[8] = {'D', 'T', 'R', 'M', 'O', 'D', 'L', '1'};
+
+int dtree_model_save(const dtree_model* m, const char* path, void* stream) {
+    if (!m || !path) return DTREE_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<unsigned char> buf;
+    auto put = [&](const void* p, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        buf.insert(buf.end(), b, b + n);
+    };
+    put(kModelMagic, 8);
+    const int32_t hdr[5] = {m->d, m->dpad, m->H, m->C, m->level};
+    put(hdr, sizeof(hdr));
+    put(&m->tree_hash, 8);
+    put(&m->t, 8);
+    put(m->mean, (size_t)m->d * 4);
+    put(m->scale, (size_t)m->d * 4);
+    for (int i = 0; i < 6; ++i) {
+        std::vector<float> h((size_t)m->size(i));
+        DT_CHECK(cudaMemcpyAsync(h.data(), m->p[i], h.size() * 4, cudaMemcpyDeviceToHost, s));
+        DT_CHECK(cudaStreamSynchronize(s));
+        put(h.data(), h.size() * 4);
+    }
+    uint64_t sum = 1469598103934665603ull;
+    for (unsigned char b : buf) {
+        sum ^= b;
+        sum *= 1099511628211ull;
+    }
+    put(&sum, 8);
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return DTREE_ERR_IO;
+    const bool ok = std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+    return (std::fclose(f) == 0 && ok) ? DTREE_OK : DTREE_ERR_IO;
+}
+
+int dtree_model_load(const char* path, const dtree_t* ref, void* stream, dtree_model** out) {
+    if (!path || !out) return DTREE_ERR_INVALID_ARG;
+    *out = nullptr;
+    // the whole file, checked before anything touches the device
+    std::vector<unsigned char> buf;
+    {
+        FILE* f = std::fopen(path, "rb");
+        if (!f) return DTREE_ERR_IO;
+        unsigned char tmp[65536];
+        size_t n;
+        while ((n = std::fread(tmp, 1, sizeof(tmp), f)) > 0) buf.insert(buf.end(), tmp, tmp + n);
+        const bool err = std::ferror(f) != 0;
+        std::fclose(f);
+        if (err) return DTREE_ERR_IO;
+    }
+    size_t at = 0;
+    auto get = [&](void* p, size_t n) {
+        if (buf.size() - at < n) return false;
+        std::memcpy(p, buf.data() + at, n);
+        at += n;
+        return true;
+    };
+    char magic[8];
+    int32_t hdr[5];
+    uint64_t hash = 0;
+    int64_t steps = 0;
+    if (buf.size() < 8 + 8 || !get(magic, 8) || std::memcmp(magic, kModelMagic, 8) != 0 ||
+        !get(hdr, sizeof(hdr)) || !get(&hash, 8) || !get(&steps, 8))
+        return DTREE_ERR_IO;
+    const int32_t d = hdr[0], dpad = hdr[1], H = hdr[2], C = hdr[3], level = hdr[4];
+    if (d < 1 || d > 64 || dpad < d || dpad > 64 || H != 256 || level < 1 || level > 30 ||
+        C != (1 << level))
+        return DTREE_ERR_IO;
+    {
+        uint64_t sum = 1469598103934665603ull, stored = 0;
+        std::memcpy(&stored, buf.data() + buf.size() - 8, 8);
+        for (size_t i = 0; i + 8 < buf.size(); ++i) {
+            sum ^= buf[i];
+            sum *= 1099511628211ull;
+        }
+        if (sum != stored) return DTREE_ERR_IO;
+    }
+    if (!ref) return DTREE_ERR_INVALID_ARG;
+    if (ref->d != d || level > ref->height) return DTREE_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t mine = 0;
+    int rc = dt::tree_fingerprint(ref, level, &mine, s);
+    if (rc != DTREE_OK) return rc;
+    if (mine != hash) return DTREE_ERR_INVALID_ARG;  // trained for another tree
+    auto* md = new (std::nothrow) dtree_model;
+    if (!md) return DTREE_ERR_OOM;
+    md->d = d;
+    md->dpad = dpad;
+    md->H = H;
+    md->C = C;
+    md->level = level;
+    md->t = steps;
+    md->tree_hash = hash;
+    cudaGetDevice(&md->device);
+    if (!get(md->mean, (size_t)d * 4) || !get(md->scale, (size_t)d * 4)) {
+        dt::model_release(md);
+        return DTREE_ERR_IO;
+    }
+    rc = dt::model_alloc(md, s);
+    for (int i = 0; i < 6 && rc == DTREE_OK; ++i) {
+        const size_t n = (size_t)md->size(i) * 4;
+        if (buf.size() - 8 < at || buf.size() - 8 - at < n) {
+            rc = DTREE_ERR_IO;
+            break;
+        }
+        if (cudaMemcpyAsync(md->p[i], buf.data() + at, n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            rc = DTREE_ERR_CUDA;
+        at += n;
+    }
+    if (rc == DTREE_OK && at + 8 != buf.size()) rc = DTREE_ERR_IO;
+    if (rc == DTREE_OK) rc = dt::refresh_half(*md, s);
+    if (rc == DTREE_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = DTREE_ERR_CUDA;
+    if (rc != DTREE_OK) {
+        cudaStreamSynchronize(s);
+        dt::model_release(md);
+        return rc;
+    }
+    *out = md;
+    return DTREE_OK;
+}
 
 int dtree_model_classes(const dtree_model* m) { return m ? m->C : -1; }
 

@@ -82,6 +82,8 @@ def _load() -> ctypes.CDLL:
     lib.dtree_debug_mma.restype = ctypes.c_int
     lib.dtree_debug_tc_timers.argtypes = [_P]
     lib.dtree_debug_tc_timers.restype = ctypes.c_int
+    lib.dtree_debug_tc_stall.argtypes = [_I32]
+    lib.dtree_debug_tc_stall.restype = ctypes.c_int
     lib.dtree_launch_count.argtypes = []
     lib.dtree_launch_count.restype = _I64
     lib.dtree_alloc_count.argtypes = []
@@ -104,6 +106,10 @@ def _load() -> ctypes.CDLL:
     lib.dtree_model_free.restype = None
     lib.dtree_model_classes.argtypes = [_P]
     lib.dtree_model_classes.restype = ctypes.c_int
+    lib.dtree_model_save.argtypes = [_P, ctypes.c_char_p, _P]
+    lib.dtree_model_save.restype = ctypes.c_int
+    lib.dtree_model_load.argtypes = [ctypes.c_char_p, _P, _P, ctypes.POINTER(_P)]
+    lib.dtree_model_load.restype = ctypes.c_int
     lib.dtree_attach_proposal.argtypes = [_P, _P]
     lib.dtree_attach_proposal.restype = ctypes.c_int
     lib.dtree_mlp_loss_grad.argtypes = [_I32, _I32, ctypes.POINTER(_P), _P, _P, _I32,
@@ -203,7 +209,7 @@ def dtree_build(points: torch.Tensor, leaf_size: int = 32, stream=None) -> Tree:
 def dtree_knn(query: Optional[Tree], ref: Tree, k: int, precision: str = "fp32",
               query_block: int = 0, seed_points: int = 0, out_idx: Optional[torch.Tensor] = None,
               out_dist: Optional[torch.Tensor] = None, stream=None, with_stats: bool = False,
-              proposal: int = 0, cap_leaves: int = 0):
+              proposal: int = 0, cap_leaves: int = 0, spin_budget: int = 0):
     """Exact kNN of every point of ``query`` (None = monochromatic) in ``ref``.
 
     Returns (idx int64 (n_q, k), dist float32 (n_q, k)) on the device, plus a
@@ -225,7 +231,7 @@ def dtree_knn(query: Optional[Tree], ref: Tree, k: int, precision: str = "fp32",
     if out_dist.shape != (nq, k) or out_dist.dtype != torch.float32 or not out_dist.is_contiguous():
         raise ValueError("out_dist must be a contiguous float32 (n_q, k) tensor")
     o = _opts(precision=PRECISIONS[precision], query_block=query_block, seed_points=seed_points,
-              proposal=proposal, cap_leaves=cap_leaves)
+              proposal=proposal, cap_leaves=cap_leaves, spin_budget=spin_budget)
     st = dtree_stats()
     rc = _lib.dtree_knn(None if query is None else query.handle, ref.handle, int(k),
                         ctypes.c_void_p(out_idx.data_ptr()), ctypes.c_void_p(out_dist.data_ptr()),
@@ -239,7 +245,7 @@ def dtree_knn(query: Optional[Tree], ref: Tree, k: int, precision: str = "fp32",
 
 def dtree_knn_batch(problems, precision: str = "fp32", query_block: int = 0,
                     seed_points: int = 0, stream=None, with_stats: bool = False,
-                    proposal: int = 0, cap_leaves: int = 0):
+                    proposal: int = 0, cap_leaves: int = 0, spin_budget: int = 0):
     """Many independent kNN problems in one call.
 
     ``problems``: a sequence of (query Tree or None, ref Tree, k) or
@@ -266,7 +272,7 @@ def dtree_knn_batch(problems, precision: str = "fp32", query_block: int = 0,
         arr[i].out_idx = oi.data_ptr() if oi.numel() else None
         arr[i].out_dist = od.data_ptr() if od.numel() else None
     o = _opts(precision=PRECISIONS[precision], query_block=query_block, seed_points=seed_points,
-              proposal=proposal, cap_leaves=cap_leaves)
+              proposal=proposal, cap_leaves=cap_leaves, spin_budget=spin_budget)
     st = dtree_stats()
     rc = _lib.dtree_knn_batch(n, arr, ctypes.byref(o), _stream(stream),
                               ctypes.byref(st) if with_stats else None)
@@ -315,6 +321,23 @@ def dtree_proposal_train(ref: Tree, train: Tree, k: int, epochs: int = 0, batch:
     if rc != DTREE_OK:
         raise DTreeError(rc, "dtree_proposal_train")
     return Model(h.value, [float(x) for x in losses])
+
+
+def dtree_model_save(model: Model, path: str, stream=None) -> None:
+    """Write a trained proposal to ``path`` (see dtree.h for the format)."""
+    rc = _lib.dtree_model_save(model.handle, os.fsencode(path), _stream(stream))
+    if rc != DTREE_OK:
+        raise DTreeError(rc, "dtree_model_save")
+
+
+def dtree_model_load(path: str, ref: Optional[Tree], stream=None) -> Model:
+    """Read a proposal saved by dtree_model_save for the reference tree ``ref``."""
+    h = _P()
+    rc = _lib.dtree_model_load(os.fsencode(path), None if ref is None else ref.handle,
+                               None if ref is None else _stream(stream), ctypes.byref(h))
+    if rc != DTREE_OK:
+        raise DTreeError(rc, "dtree_model_load")
+    return Model(h.value, [])
 
 
 def dtree_attach_proposal(ref: Tree, model: Optional[Model]) -> None:
@@ -501,10 +524,15 @@ def dtree_debug_mma(A: torch.Tensor, B: torch.Tensor, fmt: str = "bf16", stream=
     return out
 
 
-TC_TIMERS = ("plan_window", "plan_wait", "plan_stage", "conv_wait_raw", "conv_wait_slot",
-             "conv_work", "epi_wait", "epi_work", "epi_rare_chunks", "epi_finish", "item_setup",
-             "epi_tmem", "epi_hot", "epi_rare_cycles", "epi_tail", "epi_flush", "tiles", "items",
-             "inserts", "epi_wait_op", "epi_wait_bar")
+TC_TIMERS = ("plan_window", "plan_wait", "plan_stage", "epi_wait_op", "epi_wait_acc",
+             "epi_work", "epi_rare_chunks", "epi_finish", "item_setup", "tiles", "items",
+             "inserts")
+
+
+def dtree_debug_tc_stall(on: bool) -> None:
+    """Make every block of the tensor-core pass wait on a barrier that nothing
+    completes (diagnostic of the bounded waits; see include/dtree.h)."""
+    _lib.dtree_debug_tc_stall(1 if on else 0)
 
 
 def dtree_debug_tc_timers(buf: Optional[torch.Tensor]) -> None:

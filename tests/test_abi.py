@@ -81,3 +81,40 @@ def test_oracle_and_library_share_nothing():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "liboracle" not in text, f
+
+
+def _model_file(d=2, level=1, corrupt=False):
+    """A well-formed model file (see dtree_model_save) with zero weights."""
+    import struct
+    H, C, dpad = 256, 1 << level, 16
+    body = b"DTRMODL1" + struct.pack("<5i", d, dpad, H, C, level) + struct.pack("<Qq", 12345, 7)
+    body += b"\0" * (4 * 2 * d)
+    body += b"\0" * (4 * (H * dpad + H + H * H + H + C * H + C))
+    h = 1469598103934665603
+    for byte in body:
+        h = ((h ^ byte) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    data = bytearray(body + struct.pack("<Q", h))
+    if corrupt:
+        data[40] ^= 1
+    return bytes(data)
+
+
+def test_model_file_checks_need_no_gpu(lib, tmp_path):
+    P = ctypes.c_void_p
+    lib.dtree_model_load.argtypes = [ctypes.c_char_p, P, P, ctypes.POINTER(P)]
+    out = P(1)
+    assert lib.dtree_model_load(str(tmp_path / "missing.bin").encode(), None, None,
+                                ctypes.byref(out)) == -9          # DTREE_ERR_IO
+    assert out.value is None
+    f = tmp_path / "m.bin"
+    f.write_bytes(b"not a model file" * 8)
+    assert lib.dtree_model_load(str(f).encode(), None, None, ctypes.byref(out)) == -9
+    f.write_bytes(_model_file(corrupt=True))                      # checksum fails
+    assert lib.dtree_model_load(str(f).encode(), None, None, ctypes.byref(out)) == -9
+    f.write_bytes(_model_file()[:-9] + _model_file()[-8:])        # truncated
+    assert lib.dtree_model_load(str(f).encode(), None, None, ctypes.byref(out)) == -9
+    # a sound file passes every file check and then needs a tree
+    f.write_bytes(_model_file())
+    assert lib.dtree_model_load(str(f).encode(), None, None, ctypes.byref(out)) == -1
+    lib.dtree_model_save.argtypes = [P, ctypes.c_char_p, P]
+    assert lib.dtree_model_save(None, str(f).encode(), None) == -1

@@ -99,3 +99,48 @@ def test_proposal_needs_a_model(dt):
         assert e.value.status == -1
     finally:
         tr.free()
+
+
+def test_model_save_load_round_trip(dt, tmp_path):
+    W, tr, tq, tt = _setup(dt, 100_000, 10_000, 10_000)
+    tr2 = dt.dtree_build(torch.from_numpy(W.ref).cuda(), 32)
+    other = dt.dtree_build(torch.from_numpy(W.ref[::2].copy()).cuda(), 32)
+    try:
+        model = dt.dtree_proposal_train(tr, tt, W.k, epochs=5, batch=128)
+        path = tmp_path / "proposal.bin"
+        dt.dtree_model_save(model, str(path))
+        # a tree rebuilt from the same points accepts the file
+        loaded = dt.dtree_model_load(str(path), tr2)
+        assert loaded.classes == model.classes
+        # the loaded weights are the saved ones: saving them again gives the same bytes
+        again = tmp_path / "again.bin"
+        dt.dtree_model_save(loaded, str(again))
+        assert again.read_bytes() == path.read_bytes()
+        # and its searches propose the same cells: identical lists and work
+        dt.dtree_attach_proposal(tr, model)
+        dt.dtree_attach_proposal(tr2, loaded)
+        a = dt.dtree_knn(tq, tr, W.k, with_stats=True, proposal=4)
+        b = dt.dtree_knn(tq, tr2, W.k, with_stats=True, proposal=4)
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+        for key in ("seed_point_pairs", "leaf_pairs_emitted", "point_pairs"):
+            assert a[2][key] == b[2][key], key
+        ti, td = truth(W.ref, W.query, W.k)
+        compare(b[0].cpu().numpy(), b[1].cpu().numpy(), ti, td, W.k)
+        # a tree of other points rejects it; a damaged file is refused
+        with pytest.raises(dt.DTreeError) as e:
+            dt.dtree_model_load(str(path), other)
+        assert e.value.status == -1
+        raw = bytearray(path.read_bytes())
+        raw[100] ^= 0x40
+        bad = tmp_path / "bad.bin"
+        bad.write_bytes(bytes(raw))
+        with pytest.raises(dt.DTreeError) as e:
+            dt.dtree_model_load(str(bad), tr2)
+        assert e.value.status == -9
+        dt.dtree_attach_proposal(tr, None)
+        dt.dtree_attach_proposal(tr2, None)
+        loaded.free()
+        model.free()
+    finally:
+        for t in (tr, tq, tt, tr2, other):
+            t.free()
