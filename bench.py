@@ -1,19 +1,28 @@
 #!/usr/bin/env python
 """Benchmark of exact k-nearest-neighbour search (dual-tree, kd-tree, B(N_q) bound).
 
-Workload (synthetic, seeded): bichromatic kNN with N_r = 4,000,000 reference and
-N_q = 1,000,000 query points in d = 16 drawn from a 32-component isotropic
-Gaussian mixture (centres U[-10,10]^16, sigma = 1), k = 10, leaf size 32.
+Default workload (synthetic, seeded; --workload powerlaw64): bichromatic kNN
+with N_r = N_q = 2,000,000 points in d = 64 drawn from a Gaussian with a
+power-law covariance spectrum (eigenvalue i proportional to i^-1.5, random
+rotation), k = 50, leaf size 32.  The headline arm is the learned proposal
+(trained once, before the timed region, on the method's own answers for
+200,000 disjoint training queries) with split-BF16 tensor-core BaseCase tiles
+and the float64 re-rank; the same run times the same precision without the
+proposal and the plain FP32 GPU dual-tree (CUDA-core tiles) on the same
+inputs, and reports value / plain as `vs_plain_fp32`.  --workload latent3
+(10M x 1M, d = 8, k = 10) and gmm16 (4M x 1M, d = 16, k = 10) run the same
+contract.
 
 One step = the whole path: build the reference kd-tree, build the query
-kd-tree, run the exact kNN search (seed, bounds, pruning dual-tree traversal,
-BaseCase tiles, float64 re-rank, output).  `value` = queries/s of the whole job
-(all ranks' queries / the slowest rank's time).  The inputs (256 MB + 64 MB)
-exceed the 129 MB L2, so no flush is needed between steps.
+kd-tree, run the exact kNN search (seed, per-query caps, bounds, pruning
+dual-tree traversal, BaseCase tiles, float64 re-rank, output).  `value` =
+queries/s of the whole job (all ranks' queries / the slowest rank's time).
+The inputs exceed the 129 MB L2, so no flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload powerlaw64|latent3|gmm16] [--op knn|kfn|range|emst]
 
-Under torchrun each rank searches its own 1M-query shard against the same
+Under torchrun each rank searches its own query shard against the same
 reference set (weak scaling, no collective on the data path).
 """
 from __future__ import annotations
@@ -42,23 +51,34 @@ WORKLOAD = ("gmm16: bichromatic exact kNN, N_r=4,000,000, N_q=1,000,000, d=16, k
 
 
 def parse():
-    p = argparse.ArgumentParser()
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="bf16")
+    p.add_argument("--op", choices=["knn", "kfn", "range", "emst"], default="knn",
+                   help="knn (the headline), k-furthest neighbours, range search, or the "
+                        "Euclidean minimum spanning tree")
+    p.add_argument("--workload", choices=["powerlaw64", "latent3", "gmm16"], default="powerlaw64",
+                   help="kNN workload (--op knn)")
+    p.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default=None,
+                   help="BaseCase arithmetic (default: the workload's)")
+    p.add_argument("--proposal", type=int, default=None,
+                   help="learned-proposal cells per query block, 0 = none (default: the workload's)")
+    p.add_argument("--train-queries", type=int, default=200_000)
+    p.add_argument("--arm-steps", type=int, default=2,
+                   help="timed steps of the same precision without the proposal")
+    p.add_argument("--plain-steps", type=int, default=1,
+                   help="timed steps of the plain FP32 dual-tree (0 skips it)")
     p.add_argument("--leaf", type=int, default=32)
     p.add_argument("--query-block", type=int, default=0)
-    p.add_argument("--e2e-steps", type=int, default=3)
-    p.add_argument("--n-ref", type=int, default=4_000_000)
-    p.add_argument("--n-query", type=int, default=1_000_000)
-    p.add_argument("--cpu-queries", type=int, default=8192)
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--n-ref", type=int, default=0, help="override the workload's reference count")
+    p.add_argument("--n-query", type=int, default=0, help="override the workload's query count")
+    p.add_argument("--cpu-queries", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--ref-queries", type=int, default=512)
-    p.add_argument("--op", choices=["knn", "kfn", "range", "emst"], default="knn",
-                   help="knn: the headline; kfn: exact k-furthest neighbours and range: exact "
-                        "range search, on the same workload")
+    p.add_argument("--ref-queries", type=int, default=0,
+                   help="queries per step of the reference arm (default: the workload's)")
     p.add_argument("--range", type=float, nargs=2, default=[0.0, 2.5], metavar=("D_LO", "D_HI"))
     return p.parse_args()
 
@@ -124,33 +144,22 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# the CPU oracle as a reported baseline
+# the reference arm: the oracle on the host cores
 # ---------------------------------------------------------------------------
-
-def cpu_baseline(W, n_queries):
-    import oracle
-    cores = oracle.set_threads(os.cpu_count() or 1)
-    q = W.query[:n_queries]
-    t0 = time.perf_counter()
-    oracle.knn_dualtree(W.ref, q, W.k, W.leaf_size, par_depth=8)
-    dt = time.perf_counter() - t0
-    return {"value": n_queries / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"float64 serial-per-subtree kd-tree dual-tree (Alg 1-3, sound B) on the full "
-                       f"4,000,000-point reference set and the first {n_queries} queries "
-                       f"(i.i.d. sample of the 1,000,000); both tree builds included; "
-                       f"{dt:.1f} s wall")}
-
 
 def run_reference(args, rank, world):
     """The oracle on the host cores: each step answers a fresh sample of
-    `--ref-queries` queries against the full reference set by brute force
-    (the definition of the result)."""
+    queries of the same workload against its full reference set by brute
+    force (the definition of the result)."""
     if rank != 0:
         return
     import oracle
-    W = inputs.gmm16(n_ref=args.n_ref, n_query=args.n_query)
+    spec = WORKLOADS[args.workload]
+    a = argparse.Namespace(**vars(args))
+    a.train_queries = 0
+    W = spec["make"](a, 0)
     cores = oracle.set_threads(os.cpu_count() or 1)
-    nq = args.ref_queries
+    nq = args.ref_queries or max(8, min(512, int(2e9 / (len(W.ref) * W.d * 3))))
     times = []
     for step in range(args.warmup + args.steps):
         lo = (step * nq) % max(1, len(W.query) - nq)
@@ -165,61 +174,13 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "step": f"{nq}-query sample per step, brute force"},
+        "config": {"workload": spec["desc"], "step": f"{nq}-query sample per step, brute force"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{nq} queries per step vs all {len(W.ref)} references, "
+                         "sample": f"{nq} queries per step vs all {len(W.ref):,} references, "
                                    "float64 brute force (oracle_knn_brute)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
-
-
-# ---------------------------------------------------------------------------
-# roofline of the BaseCase tile kernel
-# ---------------------------------------------------------------------------
-
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one main
-# BaseCase launch, from a one-pass ncu capture of that launch on this
-# workload (4M x 1M, d = 16, k = 10), with the point pairs the launch
-# evaluated; a run's traffic is scaled by its own point pairs (the workload is
-# deterministic, so the ratio is 1 for the default run).  None where no capture
-# of the current kernel exists.
-TRAFFIC_CAPTURE = {"bf16": (2068111104, 129853296710)}
-
-
-def traffic_of(precision, pairs):
-    cap = TRAFFIC_CAPTURE.get(precision)
-    return None if cap is None else cap[0] * pairs / cap[1]
-
-
-def roofline(precision, d, pairs, ns_tile, sms, captured_workload=True):
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-        src = "of measured"
-    except (OSError, ValueError):
-        src = "of fallback"
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    secs = ns_tile * 1e-9
-    traffic = traffic_of(precision, pairs) if captured_workload else None
-    if precision == "fp32":
-        flops = 3.0 * d * pairs                  # d subtractions + d FMAs (2 flops each)
-        peak = 2.0 * 128 * sms * sm_max * 1e6 / 1e12
-        bound, kernel = "alu", "k_tile main launch (BaseCase, CUDA-core float32)"
-        psrc = f"2 x 128 FP32 lanes x {sms} SMs x {sm_max:.0f} MHz"
-    else:
-        flops = 2.0 * d * pairs                  # one multiply-add per coordinate and pair
-        bf16 = float(peaks.get("bf16_tflops_sustained", 1700.0))
-        peak = bf16 if precision == "bf16" else bf16 * 1.1 / 2.25
-        bound, kernel = "tensor", f"k_tile_tc main launch (BaseCase, tcgen05 {precision})"
-        psrc = (f"measured sustained BF16 dense {bf16:.1f} TFLOP/s ({src})"
-                + ("" if precision == "bf16" else " x 1.1/2.25 (nominal TF32:BF16)"))
-    achieved = flops / secs / 1e12 if secs > 0 else 0.0
-    return {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": traffic,
-            "peak_source": psrc, "algorithmic_flops_per_step": flops,
-            "point_pairs_per_step": pairs, "kernel_ms": ns_tile / 1e6}
 
 
 # ---------------------------------------------------------------------------
@@ -230,7 +191,8 @@ def shard_workload(args, rank):
     """Rank r searches its own query shard (an independent seeded stream)
     against the same reference set: the problem splits by queries with no
     exchange step."""
-    return inputs.gmm16(n_ref=args.n_ref, n_query=args.n_query, leaf_size=args.leaf, shard=rank)
+    return inputs.gmm16(n_ref=args.n_ref or 4_000_000, n_query=args.n_query or 1_000_000,
+                        leaf_size=args.leaf, shard=rank)
 
 
 def max_over_ranks(x, world, device):
@@ -252,27 +214,106 @@ def job_rate(world, n_per_rank, ms_max):
 # the CUDA path
 # ---------------------------------------------------------------------------
 
-def main():
-    args = parse()
-    rank, world, local = dist_env()
-    if args.op in ("kfn", "range"):
-        run_kfn(args, rank, world, local)
-        return
-    if args.op == "emst":
-        run_emst(args, rank, world, local)
-        return
-    if args.impl == "reference":
-        run_reference(args, rank, world)
-        return
+# ---------------------------------------------------------------------------
+# exact kNN (--op knn): the workloads and their arms
+# ---------------------------------------------------------------------------
+
+WORKLOADS = {
+    # the combined configuration: learned proposal + BF16 tensor-core tiles +
+    # exact re-rank, against the plain FP32 GPU dual-tree
+    "powerlaw64": {
+        "desc": ("powerlaw64: bichromatic exact kNN, N_r=2,000,000, N_q=2,000,000, d=64, k=50, "
+                 "Gaussian with power-law covariance spectrum (eigenvalue i ~ i^-1.5, random rotation)"),
+        "make": lambda a, rank: inputs.powerlaw64(n_ref=a.n_ref or 2_000_000, n_query=a.n_query or 2_000_000,
+                                                  n_train=a.train_queries, shard=rank),
+        "precision": "bf16", "proposal": 4, "cpu_queries": 256,
+    },
+    # the learned-proposal configuration at d = 8
+    "latent3": {
+        "desc": ("latent3: bichromatic exact kNN, N_r=10,000,000, N_q=1,000,000, d=8, k=10, "
+                 "3-dim latent U[0,1]^3 mapped by a seeded 8x3 linear map plus N(0,0.01^2) noise"),
+        "make": lambda a, rank: inputs.latent3(n_ref=a.n_ref or 10_000_000, n_query=a.n_query or 1_000_000,
+                                               n_train=a.train_queries, shard=rank),
+        "precision": "bf16", "proposal": 4, "cpu_queries": 8192,
+    },
+    # the 16-dimensional mixture at BF16 (no training set: no proposal)
+    "gmm16": {
+        "desc": WORKLOAD,
+        "make": lambda a, rank: inputs.gmm16(n_ref=a.n_ref or 4_000_000, n_query=a.n_query or 1_000_000,
+                                             leaf_size=a.leaf, shard=rank),
+        "precision": "bf16", "proposal": 0, "cpu_queries": 8192,
+    },
+}
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one main
+# BaseCase launch from a one-pass ncu capture, with the point pairs that launch
+# evaluated, per (workload, precision); a run's traffic is that capture's
+# bytes per pair times its own pairs.  Absent where no capture of the current
+# kernel exists.
+TRAFFIC_CAPTURE = {}
+
+
+def traffic_of(workload, precision, pairs):
+    cap = TRAFFIC_CAPTURE.get((workload, precision))
+    return None if cap is None else cap[0] * pairs / cap[1]
+
+
+def roofline(precision, d, pairs, ns_tile, sms, traffic):
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+        src = "of measured"
+    except (OSError, ValueError):
+        src = "of fallback"
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    secs = ns_tile * 1e-9
+    if precision == "fp32":
+        flops = 3.0 * d * pairs                  # d subtractions + d FMAs (2 flops each)
+        peak = 2.0 * 128 * sms * sm_max * 1e6 / 1e12
+        bound, kernel = "alu", "k_tile main launch (BaseCase, CUDA-core float32)"
+        psrc = f"2 x 128 FP32 lanes x {sms} SMs x {sm_max:.0f} MHz"
+    else:
+        flops = 2.0 * d * pairs                  # one multiply-add per coordinate and pair
+        bf16 = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        peak = bf16 if precision == "bf16" else bf16 * 1.1 / 2.25
+        bound, kernel = "tensor", f"k_tile_tc main launch (BaseCase, tcgen05 {precision})"
+        psrc = (f"measured sustained BF16 dense {bf16:.1f} TFLOP/s ({src})"
+                + ("" if precision == "bf16" else " x 1.1/2.25 (nominal TF32:BF16)"))
+    achieved = flops / secs / 1e12 if secs > 0 else 0.0
+    return {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": traffic,
+            "peak_source": psrc, "algorithmic_flops_per_step": flops,
+            "point_pairs_per_step": pairs, "kernel_ms": ns_tile / 1e6}
+
+
+def cpu_baseline(W, n_queries, desc):
+    import oracle
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    q = W.query[:n_queries]
+    t0 = time.perf_counter()
+    oracle.knn_dualtree(W.ref, q, W.k, W.leaf_size, par_depth=8)
+    dt = time.perf_counter() - t0
+    return {"value": n_queries / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"float64 kd-tree dual-tree (Alg 1-3, sound B; the oracle) on the full "
+                       f"{len(W.ref):,}-point reference set and the first {n_queries} queries "
+                       f"(an i.i.d. sample of the {len(W.query):,}) of {desc.split(':')[0]}; both "
+                       f"tree builds included; {dt:.1f} s wall")}
+
+
+def run_knn(args, rank, world, local):
     import torch
     import torch.distributed as dist
 
+    spec = WORKLOADS[args.workload]
+    precision = args.precision or spec["precision"]
+    M = spec["proposal"] if args.proposal is None else args.proposal
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1304_4327_gb300 import dtree
 
-    W = shard_workload(args, rank)
+    W = spec["make"](args, rank)
     d, k = W.d, W.k
     ref_d = torch.from_numpy(W.ref).cuda()
     q_d = torch.from_numpy(W.query).cuda()
@@ -281,22 +322,59 @@ def main():
     out_dist = torch.empty((nq, k), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step(ref, qry):
-        tr = dtree.dtree_build(ref, args.leaf)
-        tq = dtree.dtree_build(qry, args.leaf)
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # the learned proposal, trained once on the method's own answers for a
+    # disjoint training query set (outside the timed region); a tree rebuilt
+    # from the same points has the same cells, so each step attaches it
+    model, train_s, train_info = None, None, None
+    if M > 0:
+        if "train" not in W.extra:
+            raise SystemExit(f"workload {args.workload} has no training queries for a proposal")
+        t0 = time.perf_counter()
+        tr0 = dtree.dtree_build(ref_d, W.leaf_size)
+        tt0 = dtree.dtree_build(torch.from_numpy(W.extra["train"]).cuda(), W.leaf_size)
         try:
-            _, _, st = dtree.dtree_knn(tq, tr, k, precision=args.precision,
-                                       query_block=args.query_block, out_idx=out_idx,
-                                       out_dist=out_dist, with_stats=True)
+            model = dtree.dtree_proposal_train(tr0, tt0, k)
+        finally:
+            tr0.free()
+            tt0.free()
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        train_info = {"train_queries": int(len(W.extra["train"])), "cells": model.classes,
+                      "epochs": len(model.losses), "loss_first": model.losses[0],
+                      "loss_last": model.losses[-1], "seconds": train_s}
+
+    def step(ref, qry, prec=precision, nprop=M):
+        tr = dtree.dtree_build(ref, W.leaf_size)
+        tq = dtree.dtree_build(qry, W.leaf_size)
+        try:
+            if nprop > 0:
+                dtree.dtree_attach_proposal(tr, model)
+            _, _, st = dtree.dtree_knn(tq, tr, k, precision=prec, query_block=args.query_block,
+                                       out_idx=out_idx, out_dist=out_dist, with_stats=True,
+                                       proposal=nprop)
         finally:
             tr.free()
             tq.free()
         return st
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    def timed(n, warm, **kw):
+        for _ in range(warm):
+            step(ref_d, q_d, **kw)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = [step(ref_d, q_d, **kw) for _ in range(n)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1) / n, world, "cuda"), st
 
+    # the headline arm: W warm-up steps, then exactly K timed steps
     for _ in range(args.warmup):
         step(ref_d, q_d)
     props = torch.cuda.get_device_properties(local)
@@ -306,17 +384,9 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     launches0 = dtree.launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    stats = []
-    for _ in range(args.steps):
-        stats.append(step(ref_d, q_d))
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
+    ms_max, stats = timed(args.steps, 0)
     clock_info = clocks.stop()
     launches = dtree.launch_count() - launches0
-    ms_max = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
     value = job_rate(world, nq, ms_max)
 
     # end to end through the public API: pinned host inputs in, host results out
@@ -340,26 +410,42 @@ def main():
     e2e_ms = max_over_ranks(f0.elapsed_time(f1) / args.e2e_steps, world, "cuda")
     e2e_value = job_rate(world, nq, e2e_ms)
 
+    # the comparison arms on the same inputs: the same precision without the
+    # proposal, and the plain FP32 GPU dual-tree (CUDA-core tiles, no proposal)
+    arms = {}
+    if M > 0 and args.arm_steps > 0:
+        ms_tc, st_tc = timed(args.arm_steps, 1, nprop=0)
+        arms[f"{precision}_no_proposal"] = {"value": job_rate(world, nq, ms_tc), "ms_per_step": ms_tc,
+                                            "basecase_ms": st_tc[-1]["ns_basecase"] / 1e6,
+                                            "seed_ms": st_tc[-1]["ns_seed"] / 1e6,
+                                            "traverse_ms": st_tc[-1]["ns_traverse"] / 1e6}
+    if args.plain_steps > 0 and precision != "fp32":
+        ms_pl, st_pl = timed(args.plain_steps, 0, prec="fp32", nprop=0)
+        arms["plain_fp32"] = {"value": job_rate(world, nq, ms_pl), "ms_per_step": ms_pl,
+                              "basecase_ms": st_pl[-1]["ns_basecase"] / 1e6,
+                              "steps": args.plain_steps, "warmup": 0}
+
     # roofline of the dominant kernel: the main BaseCase tile launch, timed per
     # call with CUDA events on the launching stream
-    ns_tile = sum(s["ns_basecase"] for s in stats) / len(stats)
-    ns_seed = sum(s["ns_seed"] for s in stats) / len(stats)
-    ns_fb = sum(s["ns_fallback"] for s in stats) / len(stats)
-    ns_trav = sum(s["ns_traverse"] for s in stats) / len(stats)
-    pairs = sum(s["point_pairs"] for s in stats) / len(stats)
+    mean = lambda key: sum(s[key] for s in stats) / len(stats)
+    ns_tile, ns_seed, ns_fb, ns_trav = mean("ns_basecase"), mean("ns_seed"), mean("ns_fallback"), mean("ns_traverse")
+    pairs = mean("point_pairs")
     sms = props.multi_processor_count
-    roof = roofline(args.precision, d, pairs, ns_tile, sms,
-                    (args.n_ref, args.n_query, args.leaf) == (4_000_000, 1_000_000, 32))
+    roof = roofline(precision, d, pairs, ns_tile, sms, traffic_of(args.workload, precision, pairs))
     s0 = stats[-1]
+    arm_name = ("learned proposal (M=%d) + " % M if M else "") + precision.upper() + (
+        " tensor-core tiles + float64 re-rank" if precision != "fp32" else " CUDA-core tiles")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if precision == "fp32" else precision,
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": args.precision, "leaf_size": args.leaf,
-                   "query_block": args.query_block or 128,
+        "config": {"workload": spec["desc"], "arm": arm_name, "precision": precision,
+                   "proposal": M, "leaf_size": W.leaf_size, "query_block": args.query_block or 128,
                    "step": "build ref tree + build query tree + dtree_knn",
-                   "l2": "inputs (320 MB) larger than the 129 MB L2; no flush",
+                   "l2": (f"inputs ({(W.ref.nbytes + W.query.nbytes) / 1e6:.0f} MB) larger than the "
+                          "129 MB L2; no flush"),
                    "parallelism": f"{world} GPU(s), one query shard each, reference replicated"},
         "roofline": roof,
         "phases_ms": {"seed": ns_seed / 1e6, "basecase_main": ns_tile / 1e6,
@@ -370,18 +456,40 @@ def main():
                                           "leaf_pairs_evaluated", "point_pairs",
                                           "rerank_candidates", "fallback_queries",
                                           "seed_point_pairs")},
+        "arms": arms,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(W.ref.nbytes + W.query.nbytes),
                 "d2h_bytes_per_step": int(nq * k * (8 + 4))},
         "gpu_launches": int(launches),
         "clocks": clock_info,
     }
+    if "plain_fp32" in arms:
+        line["vs_plain_fp32"] = value / arms["plain_fp32"]["value"]
+    if train_info:
+        line["proposal_training"] = train_info
+    if model is not None:
+        model.free()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(W, args.cpu_queries)
+        line["cpu_baseline"] = cpu_baseline(W, args.cpu_queries or spec["cpu_queries"], spec["desc"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.op in ("kfn", "range"):
+        run_kfn(args, rank, world, local)
+        return
+    if args.op == "emst":
+        run_emst(args, rank, world, local)
+        return
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_knn(args, rank, world, local)
 
 
 # ---------------------------------------------------------------------------
@@ -415,8 +523,8 @@ def run_kfn(args, rank, world, local):
     if args.impl == "reference":
         if rank != 0:
             return
-        W = inputs.gmm16(n_ref=args.n_ref, n_query=args.n_query)
-        nq = min(args.ref_queries, 16)
+        W = inputs.gmm16(n_ref=args.n_ref or 4_000_000, n_query=args.n_query or 1_000_000)
+        nq = min(args.ref_queries or 16, 16)
         times = []
         for step in range(args.warmup + args.steps):
             lo = (step * nq) % max(1, len(W.query) - nq)
@@ -590,7 +698,7 @@ def run_emst(args, rank, world, local):
     seconds per round; see the design notes).  One problem per GPU: under
     torchrun every rank solves its own point set."""
     from oracle import emst as oemst
-    n = args.n_ref if args.n_ref != 4_000_000 else 1_000_000
+    n = args.n_ref or 1_000_000
     P = inputs.uniform(n, 3, 7 + rank)
     workload = f"emst: uniform U[0,1]^3, N={n:,}, leaf {args.leaf}"
     if args.impl == "reference":

@@ -306,9 +306,13 @@ int dtree_knn_batch(int32_t nprob, const dtree_problem* probs, const dtree_opts*
  *     are used; the call then returns DTREE_ERR_TOO_LARGE).
  * `stats` is not offered (the phase timers would create CUDA events).
  *
- * The array's address on the current device is looked up once per device
- * (cudaGetSymbolAddress, with that device current) and cached.  The trees
- * must live on the current device (else DTREE_ERR_INVALID_ARG).
+ * The array's address on the current device is looked up on every call
+ * (cudaGetSymbolAddress, with that device current; it allocates nothing), so
+ * a device reset cannot leave a stale address behind.  The trees must live on
+ * the current device (else DTREE_ERR_INVALID_ARG).  With a tensor-core
+ * precision, a reference tree whose operand rows were not made by an earlier
+ * dtree_knn call gets them in the array for this call only (they count
+ * against its size).
  *
  * The array keeps whatever the previous call left in it; every buffer whose
  * contents must start at zero (work counters, per-block pair counts,

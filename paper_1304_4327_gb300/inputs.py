@@ -155,8 +155,10 @@ def batched_problem(spec: dict, n_cap: Optional[int] = None) -> Workload:
 
 
 def latent3(n_ref: int = 10_000_000, n_query: int = 1_000_000, n_train: int = 200_000,
-            d: int = 8, k: int = 10, leaf_size: int = 32) -> Workload:
-    gp, gr, gq = _streams(4)
+            d: int = 8, k: int = 10, leaf_size: int = 32, shard: int = 0) -> Workload:
+    """``shard`` > 0 draws an independent query (and training) set."""
+    gp, gr, _ = _streams(4)
+    gq = _query_stream(4, shard)
     A = gp.standard_normal((d, 3)).astype(np.float32)
 
     def draw(g, n):
@@ -171,8 +173,11 @@ def latent3(n_ref: int = 10_000_000, n_query: int = 1_000_000, n_train: int = 20
 
 
 def powerlaw64(n_ref: int = 2_000_000, n_query: int = 2_000_000, d: int = 64, k: int = 50,
-               leaf_size: int = 32) -> Workload:
-    gp, gr, gq = _streams(5)
+               leaf_size: int = 32, n_train: int = 0, shard: int = 0) -> Workload:
+    """``n_train`` > 0 also draws a disjoint training query set (after the
+    queries, from their stream); ``shard`` > 0 draws an independent query set."""
+    gp, gr, _ = _streams(5)
+    gq = _query_stream(5, shard)
     G = gp.standard_normal((d, d))
     Q, R = np.linalg.qr(G)
     Q = Q * np.sign(np.diag(R))[None, :]
@@ -183,7 +188,12 @@ def powerlaw64(n_ref: int = 2_000_000, n_query: int = 2_000_000, d: int = 64, k:
         z = g.standard_normal((n, d), dtype=np.float32)
         return (z @ M.T).astype(np.float32)
 
-    return Workload("powerlaw64", draw(gr, n_ref), draw(gq, n_query), k, leaf_size, {"M": M})
+    ref = draw(gr, n_ref)
+    query = draw(gq, n_query)
+    extra = {"M": M}
+    if n_train > 0:
+        extra["train"] = draw(gq, n_train)
+    return Workload("powerlaw64", ref, query, k, leaf_size, extra)
 
 
 WORKLOADS = {1: mono_uniform, 2: gmm16, 3: batched_specs, 4: latent3, 5: powerlaw64}

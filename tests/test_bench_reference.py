@@ -12,8 +12,10 @@ KEYS = {"impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_
         "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"}
 
 
-@pytest.mark.parametrize("op,extra", [("knn", ["--ref-queries", "8"]), ("kfn", []), ("range", []),
-                                      ("emst", [])])
+@pytest.mark.parametrize("op,extra", [("knn", ["--ref-queries", "8"]),
+                                      ("knn", ["--workload", "latent3", "--ref-queries", "8"]),
+                                      ("knn", ["--workload", "gmm16"]),
+                                      ("kfn", []), ("range", []), ("emst", [])])
 def test_reference_arm_prints_one_line(op, extra):
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--op", op,
            "--n-ref", "3000", "--n-query", "200", "--steps", "1", "--warmup", "1", *extra]

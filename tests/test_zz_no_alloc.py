@@ -86,3 +86,27 @@ def test_rejects_sizes_beyond_the_maximum(dt):
     finally:
         tr.free()
         tq.free()
+
+
+def test_candidate_pairs_beyond_the_array_are_refused(dt):
+    # d = 64 power-law points: nearly every (query block, leaf) pair survives
+    # the bound, so 20k queries against 400k references in leaves of 4 points
+    # need far more candidate-pair storage than the array holds; the device
+    # reports it and the call returns DTREE_ERR_TOO_LARGE without allocating
+    W = inputs.powerlaw64(n_ref=400_000, n_query=20_000)
+    tr = dt.dtree_build(torch.from_numpy(W.ref).cuda(), 4)
+    tq = dt.dtree_build(torch.from_numpy(W.query).cuda(), 4)
+    try:
+        oi = torch.empty((tq.n, 5), dtype=torch.int64, device="cuda")
+        od = torch.empty((tq.n, 5), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        a0 = dt.alloc_count()
+        with pytest.raises(dt.DTreeError) as e:
+            dt.dtree_knn_noalloc(tq, tr, 5, oi, od)
+        assert e.value.status == DTREE_ERR_TOO_LARGE
+        assert dt.alloc_count() == a0
+    finally:
+        tr.free()
+        tq.free()
+    # a problem that fits still gives dtree_knn's result afterwards
+    _pair(dt, W.ref[:50_000], W.query[:5_000], 5, 32, "fp32")
