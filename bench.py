@@ -59,7 +59,7 @@ def parse():
     p.add_argument("--op", choices=["knn", "kfn", "range", "emst"], default="knn",
                    help="knn (the headline), k-furthest neighbours, range search, or the "
                         "Euclidean minimum spanning tree")
-    p.add_argument("--workload", choices=["powerlaw64", "latent3", "gmm16"], default="powerlaw64",
+    p.add_argument("--workload", choices=["powerlaw64", "latent3", "gmm16", "batched"], default="powerlaw64",
                    help="kNN workload (--op knn)")
     p.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default=None,
                    help="BaseCase arithmetic (default: the workload's)")
@@ -154,6 +154,9 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
+    if args.workload == "batched":
+        run_reference_batched(args, world)
+        return
     spec = WORKLOADS[args.workload]
     a = argparse.Namespace(**vars(args))
     a.train_queries = 0
@@ -181,6 +184,38 @@ def run_reference(args, rank, world):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def run_reference_batched(args, world):
+    """The batched workload's reference arm: each step answers a sample of
+    queries of one of the 256 problems (in turn) by brute force."""
+    import oracle
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    specs = inputs.batched_specs()
+    nq = args.ref_queries or 256
+    times, done = [], 0
+    for step in range(args.warmup + args.steps):
+        W = inputs.batched_problem(specs[step % len(specs)])
+        m = min(nq, len(W.ref))
+        t0 = time.perf_counter()
+        oracle.knn_brute(W.ref, W.ref[:m], W.k, self_idx=np.arange(m, dtype=np.int64))
+        if step >= args.warmup:
+            times.append(time.perf_counter() - t0)
+            done += m
+    t = sum(times)
+    value = done / t
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / len(times) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_BATCHED,
+                   "step": f"up to {nq} queries of one problem (in turn) per step, brute force"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"up to {nq} queries per step of problem (step mod 256) against "
+                                   "its own points, float64 brute force (oracle_knn_brute)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
 
 
 # ---------------------------------------------------------------------------
@@ -477,6 +512,167 @@ def run_knn(args, rank, world, local):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# the batched workload (--workload batched): 256 problems, one call
+# ---------------------------------------------------------------------------
+
+WORKLOAD_BATCHED = ("batched: 256 independent monochromatic exact kNN problems, N log-normal "
+                    "between 1,000 and 200,000 (6.68 M points in all), d from {3, 8, 32}, k from "
+                    "{1, 10}, uniform or Gaussian by seed, autotuned leaf size and queries per block")
+
+
+def run_batched(args, rank, world, local):
+    """One step = build every problem's tree (its tuned leaf size) + one
+    dtree_knn_batch call over all 256 problems (their tuned block sizes).
+    The tuner measures each problem class once, before the timed region.
+    The same invocation times one dtree_knn call per problem on the same
+    trees' inputs.  Under torchrun every rank solves its own copy of the
+    batch (weak scaling)."""
+    import torch
+    import torch.distributed as dist
+    from paper_1304_4327_gb300 import autotune
+
+    precision = args.precision or "fp32"
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1304_4327_gb300 import dtree
+
+    specs = inputs.batched_specs()
+    probs = [inputs.batched_problem(sp) for sp in specs]
+    pts = [torch.from_numpy(W.ref).cuda() for W in probs]
+    nq = sum(len(W.ref) for W in probs)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    t0 = time.perf_counter()
+    tuner = autotune.Autotuner(repeats=1)
+    choice = tuner.choose_batch([(p, None, W.k) for p, W in zip(pts, probs)], precision)
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
+
+    def step(points, batched=True):
+        trees = [dtree.dtree_build(p, leaf) for p, (leaf, _) in zip(points, choice)]
+        try:
+            if batched:
+                outs, st = dtree.dtree_knn_batch(
+                    [(None, tr, W.k, qb) for tr, W, (_, qb) in zip(trees, probs, choice)],
+                    precision=precision, with_stats=True)
+            else:
+                outs, st = [], None
+                for tr, W, (_, qb) in zip(trees, probs, choice):
+                    i, d = dtree.dtree_knn(None, tr, W.k, precision=precision, query_block=qb)
+                    outs.append((i, d))
+        finally:
+            for tr in trees:
+                tr.free()
+        return outs, st
+
+    def timed(n, batched=True):
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = [step(pts, batched) for _ in range(n)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1) / n, world, "cuda"), res
+
+    for _ in range(args.warmup):
+        step(pts)
+    props = torch.cuda.get_device_properties(local)
+    uuid = getattr(props, "uuid", None)
+    clocks = ClockSampler(f"GPU-{uuid}" if uuid else None)
+    clocks.start()
+    launches0 = dtree.launch_count()
+    ms_max, res = timed(args.steps)
+    clock_info = clocks.stop()
+    launches = dtree.launch_count() - launches0
+    value = job_rate(world, nq, ms_max)
+    stats = [r[1] for r in res]
+
+    # end to end: every problem's points from pinned host memory, the lists back
+    host = [torch.from_numpy(W.ref).pin_memory() for W in probs]
+    dev = [torch.empty_like(p) for p in pts]
+    barrier()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    d2h = 0
+    for _ in range(args.e2e_steps):
+        for h, dv in zip(host, dev):
+            dv.copy_(h, non_blocking=True)
+        outs, _ = step(dev)
+        back = [(i.to("cpu", non_blocking=True), d.to("cpu", non_blocking=True)) for i, d in outs]
+        d2h = sum(i.numel() * 8 + d.numel() * 4 for i, d in outs)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value = job_rate(world, nq, max_over_ranks(f0.elapsed_time(f1) / args.e2e_steps, world, "cuda"))
+    del back
+
+    # one call per problem, the same trees and parameters
+    arms = {}
+    if args.arm_steps > 0:
+        ms_one, _ = timed(args.arm_steps, batched=False)
+        arms["one_call_per_problem"] = {"value": job_rate(world, nq, ms_one), "ms_per_step": ms_one}
+
+    # roofline of the main BaseCase launches (CUDA-core float32 tiles at
+    # 3 d flops per pair), per width bucket from an untimed pass
+    flops, pairs_all = 0.0, 0
+    for dd in sorted({W.d for W in probs}):
+        sel = [i for i, W in enumerate(probs) if W.d == dd]
+        trees = [dtree.dtree_build(pts[i], choice[i][0]) for i in sel]
+        try:
+            _, stb = dtree.dtree_knn_batch([(None, tr, probs[i].k, choice[i][1]) for tr, i in zip(trees, sel)],
+                                           precision=precision, with_stats=True)
+        finally:
+            for tr in trees:
+                tr.free()
+        flops += (3.0 if precision == "fp32" else 2.0) * dd * stb["point_pairs"]
+        pairs_all += stb["point_pairs"]
+    ns_tile = sum(s["ns_basecase"] for s in stats) / len(stats)
+    sms = props.multi_processor_count
+    roof = roofline(precision, 1, 1.0, ns_tile, sms, None)
+    roof["algorithmic_flops_per_step"] = flops
+    roof["point_pairs_per_step"] = pairs_all
+    roof["achieved"] = flops / (ns_tile * 1e-9) / 1e12 if ns_tile else 0.0
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = (f"main BaseCase launches of the batch ({precision}), all width buckets"
+                      if precision == "fp32" else roof["kernel"])
+    s0 = stats[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision == "fp32" else precision,
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_BATCHED, "precision": precision,
+                   "step": "build 256 trees + one dtree_knn_batch",
+                   "l2": "inputs (80 MB) and trees below the 129 MB L2 share; each step rebuilds them",
+                   "parallelism": f"{world} GPU(s), every rank its own copy of the batch",
+                   "autotune_s": tune_s, "classes": len(tuner.table)},
+        "roofline": roof,
+        "phases_ms": {"seed": s0["ns_seed"] / 1e6, "basecase_main": ns_tile / 1e6,
+                      "traverse": s0["ns_traverse"] / 1e6, "fallback": s0["ns_fallback"] / 1e6,
+                      "build_and_rest": ms_max - (s0["ns_seed"] + ns_tile + s0["ns_traverse"] + s0["ns_fallback"]) / 1e6},
+        "counters": {k2: s0[k2] for k2 in ("leaf_pairs_emitted", "point_pairs", "fallback_queries",
+                                          "kernel_launches")},
+        "arms": arms,
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(W.ref.nbytes for W in probs)),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clock_info,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -488,6 +684,9 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batched":
+        run_batched(args, rank, world, local)
         return
     run_knn(args, rank, world, local)
 

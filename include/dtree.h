@@ -455,12 +455,12 @@ int dtree_debug_mma(const float* A, const float* B, int32_t K, int32_t precision
 
 /*
  * dtree_debug_tc_timers -- diagnostic: while `counters` (device, 64 zeroed
- * uint64, or NULL to stop) is set, the tensor-core BaseCase passes add
- * per-role clock64 cycle counts and event counts to it (window loading,
- * stage waits, stage filling, conversion, epilogue waits and work, list
- * insertions, ...): counters 0..31 for the main pass, 32..63 for the seed
- * pass.  Process-wide; not thread-safe.  (No counterpart in the paper: a
- * performance probe.)
+ * uint64, or NULL to stop) is set, the tensor-core BaseCase pass adds
+ * per-role clock64 cycle counts and event counts to counters 0..31 (window
+ * preparation, slot waits and filling, MMA-issue waits, epilogue waits and
+ * work, list insertions, tiles, items; the order of the binding's
+ * TC_TIMERS).  Process-wide; not thread-safe.  (No counterpart in the paper:
+ * a performance probe.)
  */
 int dtree_debug_tc_timers(unsigned long long* counters);
 

@@ -109,23 +109,28 @@ __global__ void k_seed(const ProbDev* probs, const int32_t* blk_prob, int nblock
     }
 }
 
-// Slots 1..M of each block's seed: its proposed cells (subtrees at the seed
-// level), skipping any cell already in the seed.
+// Slots 1..M of each block's seed: its proposed cells (subtrees at the
+// proposal's cell level), skipping any cell that overlaps the seed so far.
 __global__ void k_seed_proposal(const ProbDev* probs, const int32_t* blk_prob, int nblocks,
                                 int slots, const int32_t* cells, int M, int32_t* seed_leaf0,
                                 int32_t* seed_nleaf) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nblocks) return;
     const ProbDev& P = probs[blk_prob[g]];
-    const int span = P.hr - P.Ls;
+    const int span = P.hr - P.Lp;
     int used = 1;
     for (int m = 0; m < M && used < slots; ++m) {
-        const int l0 = cells[(int64_t)g * M + m] << span;
+        const int l0 = cells[(int64_t)g * M + m] << span, nl = 1 << span;
+        // the slots must stay disjoint (every later pass counts a seed leaf
+        // once): a cell that overlaps one already in the seed is skipped
         bool dup = false;
-        for (int s = 0; s < used; ++s) dup |= seed_leaf0[g * slots + s] == l0;
+        for (int s = 0; s < used; ++s) {
+            const int s0 = seed_leaf0[g * slots + s], sn = seed_nleaf[g * slots + s];
+            dup |= l0 < s0 + sn && s0 < l0 + nl;
+        }
         if (dup) continue;
         seed_leaf0[g * slots + used] = l0;
-        seed_nleaf[g * slots + used] = 1 << span;
+        seed_nleaf[g * slots + used] = nl;
         ++used;
     }
 }
@@ -588,13 +593,16 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int cap
         P.hr = tr->height;
         P.rleaf0 = ((int64_t)1 << P.hr) - 1;
         P.Ls = 0;
-        if (nprop > 0) {
-            // seed subtrees at the proposal's cell level, so that the greedy
-            // subtree and the proposed cells are equal or disjoint
-            P.Ls = std::min(model_level(hp[i].prop), P.hr);
-        } else {
+        {
             const int seed = std::max(hp[i].k + 1, seed_pts);
             while (P.Ls < P.hr && (m >> (P.Ls + 1)) >= seed) ++P.Ls;
+        }
+        P.Lp = nprop > 0 ? std::min(model_level(hp[i].prop), P.hr) : P.Ls;
+        if (nprop > 0 && !fmt) {
+            // the CUDA-core search evaluates the proposed cells in its seed
+            // pass: its greedy subtree is a cell too, so that the two are
+            // equal or disjoint
+            P.Ls = P.Lp;
         }
         P.qpts = tq->pts;
         P.qidx = tq->idx;
@@ -607,7 +615,6 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int cap
         P.rbeg = tr->nbeg;
         P.rcnt = tr->ncnt;
         P.rbox = tr->box;
-        P.rn = m;
         P.out_idx = hp[i].out_idx;
         P.out_dist = hp[i].out_dist;
         P.k = hp[i].k;
@@ -727,6 +734,10 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int cap
     a.seed_leaf0 = sl0;
     a.seed_nleaf = sn;
     a.seed_slots = slots;
+    // the seed pass evaluates every seed slot for the CUDA-core main pass; with
+    // the tensor cores it evaluates the greedy subtree only, and the main pass
+    // evaluates the proposed cells first, at the tensor cores' rate
+    a.seed_eval_slots = fmt ? 1 : slots;
     a.cand_d = cand_d;
     a.cand_i = cand_i;
     a.qub = qub;

@@ -50,7 +50,6 @@ struct ProbDev {
     const float* rbox;  // nodes x 2 x DP; the root box's centre is the tensor-core centring point
     const void* rops;   // tensor-core operand rows of the reference points (or null)
     int64_t rls8;       // 8-row groups per leaf in rops
-    int64_t rn;         // reference points (leaf ranges follow from it and hr)
     // outputs, rows in the caller's query order
     int64_t* out_idx;
     float* out_dist;
@@ -65,7 +64,8 @@ struct ProbDev {
     int32_t mono;
     int32_t Lb;       // level of the query blocks
     int32_t hr;       // height of the reference tree
-    int32_t Ls;       // level of the seed subtrees in the reference tree
+    int32_t Ls;       // level of the greedy seed subtree in the reference tree
+    int32_t Lp;       // level of the learned proposal's cells (the proposed seed subtrees)
     int32_t item0;    // first work item of the problem
 };
 
@@ -79,6 +79,8 @@ struct TileArgs {
     const int32_t* seed_leaf0;  // per block and seed slot: first leaf of the slot's subtree
     const int32_t* seed_nleaf;  // per block and seed slot: its leaves (0: an unused slot)
     int seed_slots;             // seed slots per block (the greedy subtree, proposed cells)
+    int seed_eval_slots;        // of those, the first this many are evaluated by the seed pass;
+                                //   the tensor-core main pass evaluates the rest first
     const int64_t* csr_off;     // per block: [off[b], off[b+1]) in csr_leaf / csr_dmin, in
                                 //   evaluation order (windows sorted by box-centre distance)
     const int32_t* csr_leaf;
@@ -127,6 +129,13 @@ int launch_tc_ops(const dtree_t* t, int fmt, int ls, void* out, cudaStream_t s);
 __device__ __forceinline__ int seed_count(const int32_t* sn, int slots, int blk) {
     int t = 0;
     for (int s = 0; s < slots; ++s) t += sn[blk * slots + s];
+    return t;
+}
+
+// Leaves of a block's first n seed slots.
+__device__ __forceinline__ int seed_count_n(const int32_t* sn, int slots, int n, int blk) {
+    int t = 0;
+    for (int s = 0; s < n; ++s) t += sn[blk * slots + s];
     return t;
 }
 

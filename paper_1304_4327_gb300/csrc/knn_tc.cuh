@@ -106,23 +106,24 @@ template <int FMT, int DP, int KC, int NG>
 struct TcSmem {
     using S = TcShape<FMT, DP>;
     static constexpr int NB = 4;                                     // operand slots
-    static constexpr int WIN = 512;                                  // candidates per window
+    static constexpr int WIN = 256;                                  // candidates per window
     static constexpr int CB = 8;                                     // deferred insertions per thread
     static constexpr int OFF_A = 0;                                  // 128 x RB
     static constexpr int OFF_B = OFF_A + kQB * S::RB;                // NB x TN x RB
-    static constexpr int OFF_POS = OFF_B + NB * S::TN * S::RB;       // (NB + 2) x TN int
-    static constexpr int OFF_WIN = OFF_POS + (NB + 2) * S::TN * 4;   // 2 x WIN (leaf int, d_min float)
-    static constexpr int OFF_SCR = OFF_WIN + 2 * WIN * 8;            // NG x 32 x 128 float
+    static constexpr int OFF_GRP = OFF_B + NB * S::TN * S::RB;       // NB x TN8 int2 (row groups)
+    static constexpr int OFF_WIN = OFF_GRP + NB * S::TN8 * 8;        // 2 x WIN (leaf int, d_min float)
+    static constexpr int OFF_WENT = OFF_WIN + 2 * WIN * 8;           // WIN int4 (begin, count, leaf, group0)
+    static constexpr int OFF_SCR = OFF_WENT + WIN * 16;              // NG x 32 x 128 float
     static constexpr int OFF_BUF = OFF_SCR + NG * 32 * kQB * 4;      // NG x CB x 128 (float, int)
     static constexpr int OFF_CEN = OFF_BUF + NG * CB * kQB * 8;      // DP float
     static constexpr int END = OFF_CEN + DP * 4;
-    // at a block's end everything above is idle: the merge of the two
-    // groups' lists (float + int per entry) and the float64 re-rank (double
-    // + int per entry) reuse it from offset 0
+    // at a block's end everything above is idle: the merge of two groups'
+    // lists (float + int per entry) and the float64 re-rank (double + int per
+    // entry) reuse it from offset 0
     static constexpr int FIN = kQB * KC * 12;
     static constexpr int BYTES = END > FIN ? END : FIN;
     static_assert(BYTES <= 225 * 1024, "tensor-core tile shared memory over budget");
-    static_assert(S::TN8 * 8 == S::TN, "tiles hold whole 8-row groups");
+    static_assert(S::TN8 * 8 == S::TN && S::TN8 <= 32, "tiles hold whole 8-row groups, one per lane");
 };
 
 template <int FMT, int DP>
@@ -284,16 +285,17 @@ struct TcExtra {
 // spin_budget.
 constexpr int kDrainPolls = 1 << 22;
 
-// Diagnostic cycle counters of the tile kernel (summed over CTAs).
+// Diagnostic cycle counters of the tile kernel (summed over CTAs; read only
+// when timers are attached).
 enum TcTimer {
-    TT_PLAN_WINDOW = 0,  // planner: loading candidate windows
+    TT_PLAN_WINDOW = 0,  // planner: loading and preparing candidate windows
     TT_PLAN_WAIT,        // planner: waiting for a free operand slot
     TT_PLAN_STAGE,       // planner: filling slots and issuing copies
-    TT_EPI_WAIT_OP,      // epilogue (warp 0): waiting for a filled operand slot
-    TT_EPI_WAIT_ACC,     // epilogue (warp 0): waiting for an accumulator
+    TT_MMA_WAIT,         // MMA warp: waiting for a filled slot or a free accumulator
+    TT_EPI_WAIT,         // epilogue (warp 0): waiting for an accumulator
     TT_EPI_WORK,         // epilogue (warp 0): reading TMEM, keys, insertion
     TT_EPI_RARE,         // epilogue (all threads): chunks that took the insertion path
-    TT_EPI_FINISH,       // epilogue: merge, re-rank, output
+    TT_EPI_FINISH,       // epilogue: re-rank, output
     TT_ITEM_SETUP,       // all: query conversion, list init
     TT_TILES,            // planner: tiles produced
     TT_ITEMS,            // items processed
@@ -302,61 +304,49 @@ enum TcTimer {
 };
 static_assert(TT_N <= 32, "the diagnostic timer buffer holds 32 counters");
 
-// Named barriers of the kernel (0 is __syncthreads).
-enum { BAR_EPI = 1, BAR_G0 = 3, BAR_G1 = 4 };
-
-// Range [begin, begin + count) of leaf `leaf` of a balanced tree of n points
-// and height h: every split puts floor(count / 2) points on the left (the
-// layout the tree build writes).
-__device__ __forceinline__ int2 leaf_range(int64_t n, int h, int leaf) {
-    int64_t b = 0, c = n;
-    for (int l = h - 1; l >= 0; --l) {
-        const int64_t nl = c >> 1;
-        if ((leaf >> l) & 1) {
-            b += nl;
-            c -= nl;
-        } else {
-            c = nl;
-        }
-    }
-    return make_int2((int)b, (int)c);
-}
-
-// One persistent CTA per SM:
-//   warps 0 .. 4 NG - 1   NG epilogue groups of 4 warps: one query row (TMEM
-//                         lane) per thread; with NG = 2 the groups take
-//                         alternate tiles, each with its own accumulator and
-//                         list, merged when the block is done; with NG = 1
-//                         the group keeps two accumulators and issues the MMA
-//                         of the next tile before it reads the current one
-//   warp 4 NG             planner: walks the block's candidate leaves
-//                         nearest-first, skips those whose d_min exceeds the
-//                         block's bound (Algorithm 3) and bulk-copies the
-//                         operand rows of the rest (TMA) into NB slots
-// Hand-over by mbarriers: op_full (planner -> group: its arrival plus the
-// copied bytes), op_empty (group -> planner: the MMA's commit plus the
-// group's release), acc_full (the MMA's commit -> group).  Every wait is
-// bounded; after a failed wait the item's work is abandoned, the kernel
-// drains its own copies and MMAs, releases TMEM and reports through x.err.
+// One persistent CTA per SM, 4 NG + 2 warps:
+//   warps 0 .. 4 NG - 1  NG epilogue groups of four warps: one query row (TMEM
+//              lane) per thread; each warp reads its own 32 lanes of an
+//              accumulator, examines the keys and keeps its queries' lists,
+//              and hands the accumulator and the operand slot back by mbarrier
+//              arrivals, independently of the other warps.  Tiles alternate
+//              between two accumulators: with NG = 1 the group reads both in
+//              turn; with NG = 2 group g reads accumulator g and keeps its own
+//              lists, which are merged when the block is done
+//   warp 4 NG  planner: prepares a window of the block's candidate leaves at
+//              a time (Algorithm 3's test against the block's bound, each
+//              kept leaf's range and its place in the window's run of 8-row
+//              groups), then fills operand slots with whole 8-row groups by
+//              bulk copies (TMA) of the leaves' operand rows
+//   warp 4 NG + 1  MMA issuer: one thread turns a filled slot into an
+//              accumulator (two in turn) with tcgen05.mma
+// Hand-over by mbarriers: op_full (planner -> MMA: its arrival plus the
+// copied bytes), acc_full (MMA -> epilogue: the MMA's commit plus the
+// issuer's arrival with the tile's slot and columns), acc_empty (epilogue ->
+// MMA: one arrival per warp once its lanes are read), op_empty (MMA commit
+// and the four epilogue warps -> planner).  Every wait is bounded; after a
+// failed wait the item's work is abandoned, the kernel drains its own copies
+// and MMAs, releases TMEM and reports through x.err.
 template <int FMT, int DP, int KC, int NG>
-__global__ void __launch_bounds__(NG * 128 + 32, 1) k_tile_tc(const TileArgs a, const TcExtra x) {
+__global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs a, const TcExtra x) {
     using S = TcShape<FMT, DP>;
     using L = TcSmem<FMT, DP, KC, NG>;
     using Bd = TcBound<FMT, DP>;
-    constexpr int TN = S::TN, TN8 = S::TN8, NB = L::NB, CB = L::CB;
-    constexpr int PW = 4 * NG;  // the planner's warp
+    constexpr int TN = S::TN, TN8 = S::TN8, NB = L::NB, CB = L::CB, WIN = L::WIN;
+    constexpr int PW = 4 * NG, MW = 4 * NG + 1;  // the planner's and the MMA issuer's warps
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem + L::OFF_A;
     unsigned char* sB = smem + L::OFF_B;
-    int32_t* spos = reinterpret_cast<int32_t*>(smem + L::OFF_POS);
+    int2* sgrp = reinterpret_cast<int2*>(smem + L::OFF_GRP);   // NB x TN8
     int32_t* swleaf = reinterpret_cast<int32_t*>(smem + L::OFF_WIN);
-    float* swdmin = reinterpret_cast<float*>(smem + L::OFF_WIN + 2 * L::WIN * 4);
+    float* swdmin = reinterpret_cast<float*>(smem + L::OFF_WIN + 2 * WIN * 4);
+    int4* went = reinterpret_cast<int4*>(smem + L::OFF_WENT);
     float* sscr = reinterpret_cast<float*>(smem + L::OFF_SCR);
     float* sbuf = reinterpret_cast<float*>(smem + L::OFF_BUF);
     float* scen = reinterpret_cast<float*>(smem + L::OFF_CEN);
-    __shared__ uint64_t acc_full[2], op_full[NB], op_empty[NB], never;
+    __shared__ uint64_t op_full[NB], op_empty[NB], acc_full[2], acc_empty[2], never;
     __shared__ int ometa[NB];
-    __shared__ volatile int s_gfail[2];
+    __shared__ int2 amet[2];  // the tile in each accumulator: (slot, columns), columns < 0 ends the block
     __shared__ uint32_t s_tmem;
     __shared__ int s_item;
     __shared__ ProbDev s_prob;
@@ -364,36 +354,35 @@ __global__ void __launch_bounds__(NG * 128 + 32, 1) k_tile_tc(const TileArgs a, 
     __shared__ volatile float s_wmax[4 * NG], s_wmin[4 * NG];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int role = warp < 4 ? 0 : warp < PW ? 1 : 2;  // epilogue group 0 / 1, planner
-    const int qt = tid & 127;                           // query row of an epilogue thread
+    const bool epi = warp < 4 * NG;
+    const int grp_id = warp >> 2;  // an epilogue thread's group
+    const int qt = tid & 127;  // query row of an epilogue thread
     const int nitems = a.nitems;
     unsigned long long n_skip = 0, n_eval = 0, n_pp = 0, n_re = 0, n_ins = 0;
 
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) tc::mbar_init(&acc_full[i], 1);  // tcgen05.commit
         for (int i = 0; i < NB; ++i) {
             tc::mbar_init(&op_full[i], 1);   // the planner's arrival (+ copied bytes)
-            tc::mbar_init(&op_empty[i], 2);  // tcgen05.commit + the consuming group's release
+            tc::mbar_init(&op_empty[i], 5);  // tcgen05.commit + the four epilogue warps
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&acc_full[i], 2);   // tcgen05.commit + the issuer's arrival
+            tc::mbar_init(&acc_empty[i], 4);  // the four epilogue warps
         }
         tc::mbar_init(&never, 1);  // nothing arrives on it (the stall diagnostic)
-        s_gfail[0] = 0;
-        s_gfail[1] = 0;
         tc::fence_mbar_init();
         s_fail = 0;
     }
-    if (warp == PW) tc::tmem_alloc(&s_tmem, 2 * TN);
+    if (warp == MW) tc::tmem_alloc(&s_tmem, 2 * TN);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = s_tmem;
     const uint32_t idesc = tc::idesc(TcFmt<FMT>::hw, kQB, TN);
     // the barriers' phases carry over from item to item, so the counters do too
-    uint32_t otile = 0;         // planner: operand slot uses filled
-    uint32_t ctile = role;      // epilogue group: its next slot use (groups alternate)
-    uint32_t issued = 0, done = 0;  // epilogue group: tiles whose MMA was issued / read back
-    // accumulator of the group's j-th tile, and the parity of its completion
-    auto acc_of = [&](uint32_t j) -> int { return NG == 1 ? (int)(j & 1u) : role; };
-    auto par_of = [&](uint32_t j) -> uint32_t { return NG == 1 ? (j >> 1) & 1u : j & 1u; };
+    uint32_t otile = 0;                  // planner / MMA issuer: operand slot uses
+    uint32_t ause[2] = {0u, 0u};         // MMA issuer / each epilogue warp: uses of each accumulator
+    uint32_t acur = 0;                   // MMA issuer / each epilogue warp: the next accumulator
 
     const ProbDev& P = s_prob;
     for (;;) {
@@ -412,11 +401,11 @@ __global__ void __launch_bounds__(NG * 128 + 32, 1) k_tile_tc(const TileArgs a, 
             __syncthreads();
             continue;
         }
-        long long tm0 = clock64();
+        long long tm0 = x.timers ? clock64() : 0;
         // the centring point: the reference root box's centre, as k_tc_ops used it
         if (tid < DP) scen[tid] = 0.5f * (P.rbox[tid] + P.rbox[DP + tid]);
         __syncthreads();
-        const bool act = role < 2 && qt < nq;
+        const bool act = epi && qt < nq;
         const int myq = P.qbeg[qnode] + chunk * kQB + qt;
         const int kq = P.k;  // read once: stores below could alias P
         const bool mono = P.mono != 0;
@@ -426,8 +415,8 @@ __global__ void __launch_bounds__(NG * 128 + 32, 1) k_tile_tc(const TileArgs a, 
         const float qc = act && a.qcap ? a.qcap[P.q0 + myq] : INFINITY;
         float ld[KC];
         int li[KC];
-        if (role < 2) {
-            // the query, centred and rounded (group 0 writes row qt of the A tile)
+        if (epi) {
+            // the query, centred and rounded, as row qt of the A tile
             float h[DP];
             float qa2 = 0.f;
             const float4* q4 = reinterpret_cast<const float4*>(P.qpts + (int64_t)myq * DP);
@@ -445,7 +434,7 @@ __global__ void __launch_bounds__(NG * 128 + 32, 1) k_tile_tc(const TileArgs a, 
                 qa2 = __fmaf_ru(h[j], h[j], qa2);
             }
             qn = tc_norm<FMT, DP>(h);
-            if (role == 0) {
+            if (grp_id == 0) {
 #pragma unroll
                 for (int c = 0; c < S::NCH; ++c)
                     *reinterpret_cast<uint4*>(sA + tc::core_offset(qt, c, S::GB)) =
@@ -476,153 +465,147 @@ __global__ void __launch_bounds__(NG * 128 + 32, 1) k_tile_tc(const TileArgs a, 
             atomicAdd(&x.timers[TT_ITEMS], 1ull);
         }
 
-        if (role == 2) {
+        if (warp == PW) {
             // ================= planner =================
             const float Bq = a.Bn ? a.Bn[P.node0 + qnode] : INFINITY;
             const int64_t c0 = a.csr_off[blk], c1 = a.csr_off[blk + 1];
-            const int64_t ntot = c1 - c0;
+            // the candidates: the block's proposed cells the seed pass left
+            // (first, for a tight bound early), then the traversal's list
+            const int sn0 = seed_count_n(a.seed_nleaf, a.seed_slots, a.seed_eval_slots, blk);
+            const int npro = seed_count(a.seed_nleaf, a.seed_slots, blk) - sn0;
+            const int64_t ntot = npro + (c1 - c0);
             const unsigned char* rops = static_cast<const unsigned char*>(P.rops);
             const int64_t ls8 = P.rls8;
-            const int64_t rn = P.rn;
-            const int hr = P.hr;
             bool fail = false;
             // window w's leaves and d_min land in buffer w & 1 by cp.async,
             // issued while the previous window is processed
             auto fetch = [&](int64_t w0, int buf) {
-                const int wn = (int)(ntot - w0 < L::WIN ? ntot - w0 : L::WIN);
+                const int wn = (int)(ntot - w0 < WIN ? ntot - w0 : WIN);
                 for (int i = lane; i < wn; i += 32) {
-                    tc::cp_async4(swleaf + buf * L::WIN + i, a.csr_leaf + c0 + w0 + i);
-                    tc::cp_async4(swdmin + buf * L::WIN + i, a.csr_dmin + c0 + w0 + i);
+                    const int64_t ci = w0 + i - npro;  // entry of the traversal's list
+                    if (ci >= 0) {
+                        tc::cp_async4(swleaf + buf * WIN + i, a.csr_leaf + c0 + ci);
+                        tc::cp_async4(swdmin + buf * WIN + i, a.csr_dmin + c0 + ci);
+                    }
                 }
                 tc::cp_async_commit();
             };
             if (ntot > 0) fetch(0, 0);
             int wbuf = 0;
-            for (int64_t w0 = 0; w0 < ntot && !fail; w0 += L::WIN, wbuf ^= 1) {
-                const int wn = (int)(ntot - w0 < L::WIN ? ntot - w0 : L::WIN);
-                long long t0 = clock64();
+            for (int64_t w0 = 0; w0 < ntot && !fail; w0 += WIN, wbuf ^= 1) {
+                const int wn = (int)(ntot - w0 < WIN ? ntot - w0 : WIN);
+                long long t0 = x.timers ? clock64() : 0;
                 tc::cp_async_wait_all();
                 __syncwarp();
-                if (w0 + L::WIN < ntot) fetch(w0 + L::WIN, wbuf ^ 1);
+                if (w0 + WIN < ntot) fetch(w0 + WIN, wbuf ^ 1);
+                // the block's bound from the epilogue warps' published values
+                float b = Bq;
+#pragma unroll
+                for (int g = 0; g < NG; ++g) {
+                    float mx = -INFINITY, mn = INFINITY;
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        mx = fmaxf(mx, s_wmax[4 * g + w]);
+                        mn = fminf(mn, s_wmin[4 * g + w]);
+                    }
+                    b = fminf(b, fminf(mx, __fadd_ru(mn, lam2)));
+                }
+                // the window's kept leaves (Algorithm 3: a leaf whose d_min
+                // exceeds the bound is pruned), their ranges, and where each
+                // starts in the window's run of 8-row groups
+                // (every entry's range is read first, so the loads overlap)
+                constexpr int NR = WIN / 32;
+                int eleaf[NR], ebeg[NR], ecnt[NR];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const int i = r * 32 + lane;
+                    const bool pro = w0 + i < npro;  // a proposed cell's leaf (never pruned)
+                    const bool keep = i < wn && (pro || !(swdmin[wbuf * WIN + i] > b));
+                    eleaf[r] = !keep ? -1
+                               : pro ? seed_leaf(a.seed_leaf0, a.seed_nleaf, a.seed_slots, blk, sn0 + (int)(w0 + i))
+                                     : swleaf[wbuf * WIN + i];
+                    ebeg[r] = keep ? P.rbeg[P.rleaf0 + eleaf[r]] : 0;
+                    ecnt[r] = keep ? P.rcnt[P.rleaf0 + eleaf[r]] : 0;
+                }
+                int G = 0;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const int i = r * 32 + lane;
+                    const bool valid = i < wn;
+                    const int g = (ecnt[r] + 7) >> 3;
+                    int4 e = make_int4(ebeg[r], ecnt[r], eleaf[r], 0);
+                    int incl = g;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+                        if (lane >= off) incl += v;
+                    }
+                    e.w = G + incl - g;
+                    if (valid) went[i] = e;
+                    const unsigned kept = __ballot_sync(0xffffffffu, valid && g > 0);
+                    const unsigned all = __ballot_sync(0xffffffffu, valid);
+                    if (lane == 0) {
+                        n_eval += __popc(kept);
+                        n_skip += __popc(all & ~kept);
+                    }
+                    G += __shfl_sync(0xffffffffu, incl, 31);
+                }
+                __syncwarp();
                 if (x.timers && lane == 0)
                     atomicAdd(&x.timers[TT_PLAN_WINDOW], (unsigned long long)(clock64() - t0));
-                const int32_t* wleaf = swleaf + wbuf * L::WIN;
-                const float* wdmin = swdmin + wbuf * L::WIN;
-                int cur = 0, part = 0;  // part: groups of leaf `cur` already staged
-                bool have_slot = false;
-                int op = 0;
-                while (cur < wn) {
-                    if (!have_slot) {
-                        op = (int)(otile % NB);
-                        const uint32_t use = otile / NB;
-                        long long t1 = clock64();
-                        bool ok = lane == 0 ? tc::mbar_wait(&op_empty[op], (use & 1u) ^ 1u, x.spin_budget) : true;
-                        if (!__all_sync(0xffffffffu, ok)) {
-                            fail = true;
-                            break;
-                        }
-                        if (x.timers && lane == 0)
-                            atomicAdd(&x.timers[TT_PLAN_WAIT], (unsigned long long)(clock64() - t1));
-                        have_slot = true;
+                // tiles of TN8 groups; the entries overlapping a tile are consecutive
+                int cur = 0;
+                for (int g0 = 0; g0 < G; g0 += TN8) {
+                    const int g1 = min(g0 + TN8, G);
+                    const int op = (int)(otile % NB);
+                    const uint32_t use = otile / NB;
+                    long long t1 = x.timers ? clock64() : 0;
+                    const bool ok = lane == 0 ? tc::mbar_wait(&op_empty[op], (use & 1u) ^ 1u, x.spin_budget) : true;
+                    if (!__all_sync(0xffffffffu, ok)) {
+                        fail = true;
+                        break;
                     }
-                    long long t2 = clock64();
-                    // the block's bound from every epilogue warp's published values
-                    float b = Bq;
-#pragma unroll
-                    for (int g = 0; g < NG; ++g) {
-                        float mx = -INFINITY, mn = INFINITY;
-#pragma unroll
-                        for (int w = 0; w < 4; ++w) {
-                            mx = fmaxf(mx, s_wmax[4 * g + w]);
-                            mn = fminf(mn, s_wmin[4 * g + w]);
-                        }
-                        b = fminf(b, fminf(mx, __fadd_ru(mn, lam2)));
-                    }
+                    long long t2 = x.timers ? clock64() : 0;
+                    if (lane == 0) tc::mbar_expect_tx(&op_full[op], (uint32_t)(g1 - g0) * S::GB);
+                    __syncwarp();
                     unsigned char* slot = sB + op * TN * S::RB;
-                    int32_t* pos = spos + op * TN;
-                    int nst8 = 0;  // 8-row groups staged in the slot
-                    // rounds of 32 candidates until the slot is full or the window ends
-                    while (cur < wn && nst8 < TN8) {
-                        const int c = cur + lane;
-                        const bool valid = c < wn;
-                        int lb = 0, lc = 0, lg = 0, leaf = 0, g0 = 0;
-                        bool keep = false;
-                        if (valid) {
-                            keep = !(wdmin[c] > b);
-                            if (keep) {
-                                leaf = wleaf[c];
-                                const int2 rr = leaf_range(rn, hr, leaf);
-                                lb = rr.x;
-                                lc = rr.y;
-                                lg = (lc + 7) >> 3;
+                    int2* grp = sgrp + op * TN8;
+                    for (;;) {
+                        const int i = cur + lane;
+                        const bool valid = i < wn;
+                        const int4 e = valid ? went[i] : make_int4(0, 0, 0, 0x7fffffff);
+                        const int gs = e.w, gg = (e.y + 7) >> 3;
+                        const int lo = max(gs, g0), hi = min(gs + gg, g1);
+                        int real = 0;
+                        if (valid && hi > lo) {
+                            tc::bulk_g2s(slot + (lo - g0) * S::GB,
+                                         rops + ((int64_t)e.z * ls8 + (lo - gs)) * S::GB,
+                                         (uint32_t)(hi - lo) * S::GB, &op_full[op]);
+                            for (int q = lo; q < hi; ++q) {
+                                const int r0 = 8 * (q - gs);
+                                grp[q - g0] = make_int2(e.x + r0, min(8, e.y - r0));
                             }
+                            real = min(e.y, 8 * (hi - gs)) - 8 * (lo - gs);
                         }
-                        if (lane == 0 && part > 0 && keep) {  // rest of a split leaf
-                            g0 = part;
-                            lg -= part;
-                        }
-                        int incl = lg;
-#pragma unroll
-                        for (int off = 1; off < 32; off <<= 1) {
-                            int v = __shfl_up_sync(0xffffffffu, incl, off);
-                            if (lane >= off) incl += v;
-                        }
-                        const int excl = incl - lg;
-                        const int take = min(max(TN8 - nst8 - excl, 0), lg);
-                        const bool fullc = valid && take == lg;
-                        const unsigned fm = __ballot_sync(0xffffffffu, fullc);
-                        const int nlead = fm == 0xffffffffu ? 32 : __ffs(~fm) - 1;
-                        const bool put = take > 0 && lane <= nlead;
-                        const unsigned sk = __ballot_sync(0xffffffffu, valid && !keep && lane < nlead);
-                        const unsigned ev = __ballot_sync(0xffffffffu, keep && lane < nlead);
-                        // real points among the rows taken (the rest are padding)
-                        int real = put ? max(0, min(lc, 8 * (g0 + take)) - 8 * g0) : 0;
-                        int taken = put ? take : 0;
-#pragma unroll
-                        for (int off = 16; off > 0; off >>= 1) {
-                            taken += __shfl_xor_sync(0xffffffffu, taken, off);
-                            real += __shfl_xor_sync(0xffffffffu, real, off);
-                        }
-                        if (lane == 0) {
-                            n_skip += __popc(sk);
-                            n_eval += __popc(ev);
-                            n_pp += (unsigned long long)real * nq;
-                            if (taken) tc::mbar_expect_tx(&op_full[op], (uint32_t)taken * S::GB);
-                        }
-                        __syncwarp();
-                        if (put) {
-                            tc::bulk_g2s(slot + (nst8 + excl) * S::GB,
-                                         rops + ((int64_t)leaf * ls8 + g0) * S::GB,
-                                         (uint32_t)take * S::GB, &op_full[op]);
-                            int32_t* pp = pos + (nst8 + excl) * 8;
-                            for (int i = 0; i < 8 * take; ++i) {
-                                const int r = 8 * g0 + i;
-                                pp[i] = r < lc ? lb + r : kEmptyIdx;
-                            }
-                        }
-                        nst8 += taken;
-                        const int pn = __shfl_sync(0xffffffffu, take, nlead & 31);
-                        if (nlead < 32) {
-                            part = (nlead == 0 ? part : 0) + pn;
-                            cur += nlead;
-                            if (!(cur < wn)) part = 0;
-                            break;
-                        }
-                        cur += 32;
-                        part = 0;
+                        real = __reduce_add_sync(0xffffffffu, real);
+                        if (lane == 0) n_pp += (unsigned long long)real * nq;
+                        // entries that end within this tile are done; they form a prefix
+                        const unsigned fin = __ballot_sync(0xffffffffu, valid && gs + gg <= g1);
+                        const int adv = fin == 0xffffffffu ? 32 : __ffs(~fin) - 1;
+                        cur += adv;
+                        if (adv < 32) break;
                     }
-                    if (nst8 > 0) {
-                        if (lane == 0) ometa[op] = nst8 * 8;
-                        __syncwarp();
-                        if (lane == 0) {
-                            tc::mbar_arrive(&op_full[op], 1);
-                            if (x.timers) atomicAdd(&x.timers[TT_TILES], 1ull);
+                    if (lane == 0) ometa[op] = (g1 - g0) * 8;
+                    __syncwarp();
+                    if (lane == 0) {
+                        tc::mbar_arrive(&op_full[op], 1);
+                        if (x.timers) {
+                            atomicAdd(&x.timers[TT_TILES], 1ull);
+                            atomicAdd(&x.timers[TT_PLAN_WAIT], (unsigned long long)(t2 - t1));
+                            atomicAdd(&x.timers[TT_PLAN_STAGE], (unsigned long long)(clock64() - t2));
                         }
-                        ++otile;
-                        have_slot = false;
                     }
-                    if (x.timers && lane == 0)
-                        atomicAdd(&x.timers[TT_PLAN_STAGE], (unsigned long long)(clock64() - t2));
+                    ++otile;
                 }
             }
             // a window fetch still in flight (after a failure) lands before the
@@ -635,341 +618,321 @@ __global__ void __launch_bounds__(NG * 128 + 32, 1) k_tile_tc(const TileArgs a, 
                 const bool ok = lane == 0 ? tc::mbar_wait(&never, 0u, x.spin_budget) : true;
                 if (!__all_sync(0xffffffffu, ok)) fail = true;
             }
-            // the end of the block: one end marker for each epilogue group
-            for (int e = 0; e < NG && !fail; ++e) {
+            // the end of the block
+            if (!fail) {
                 const int op = (int)(otile % NB);
                 const uint32_t use = otile / NB;
-                bool ok = lane == 0 ? tc::mbar_wait(&op_empty[op], (use & 1u) ^ 1u, x.spin_budget) : true;
-                if (!__all_sync(0xffffffffu, ok)) {
+                const bool ok = lane == 0 ? tc::mbar_wait(&op_empty[op], (use & 1u) ^ 1u, x.spin_budget) : true;
+                if (__all_sync(0xffffffffu, ok)) {
+                    if (lane == 0) {
+                        ometa[op] = -1;
+                        tc::mbar_arrive(&op_full[op], 1);
+                    }
+                    ++otile;
+                } else {
                     fail = true;
-                    break;
                 }
-                if (lane == 0) {
-                    ometa[op] = -1;
-                    tc::mbar_arrive(&op_full[op], 1);
-                }
-                ++otile;
             }
             if (fail && lane == 0) s_fail = 1;
+        } else if (warp == MW) {
+            // ================= MMA issuer (one thread) =================
+            if (lane == 0) {
+                for (;;) {
+                    const int op = (int)(otile % NB);
+                    const uint32_t use = otile / NB;
+                    long long t0 = x.timers ? clock64() : 0;
+                    if (!tc::mbar_wait(&op_full[op], use & 1u, x.spin_budget)) {
+                        s_fail = 1;
+                        break;
+                    }
+                    const int nst = ometa[op];
+                    ++otile;
+                    if (nst < 0) {
+                        // the end of the block: nothing reads the slot; the
+                        // accumulators carry the marker to each epilogue group
+                        tc::mbar_arrive(&op_empty[op], 5);
+                        bool ok = true;
+                        for (int e = 0; e < NG && ok; ++e) {
+                            const int b = (int)acur;
+                            ok = tc::mbar_wait(&acc_empty[b], (ause[b] & 1u) ^ 1u, x.spin_budget);
+                            if (ok) {
+                                amet[b] = make_int2(op, -1);
+                                tc::mbar_arrive(&acc_full[b], 2);
+                                ++ause[b];
+                                acur ^= 1u;
+                            }
+                        }
+                        if (!ok) s_fail = 1;
+                        break;
+                    }
+                    const int b = (int)acur;
+                    if (!tc::mbar_wait(&acc_empty[b], (ause[b] & 1u) ^ 1u, x.spin_budget)) {
+                        s_fail = 1;
+                        break;
+                    }
+                    if (x.timers) atomicAdd(&x.timers[TT_MMA_WAIT], (unsigned long long)(clock64() - t0));
+                    tc::fence_after_sync();
+                    const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB + op * TN * S::RB);
+#pragma unroll
+                    for (int m = 0; m < S::NK; ++m)
+                        tc::mma<TcFmt<FMT>::hw>(tmem + (uint32_t)(b * TN),
+                                                tc::sdesc(a0 + 256u * S::astep(m), 128u, S::GB),
+                                                tc::sdesc(b0 + 256u * S::bstep(m), 128u, S::GB), idesc,
+                                                m > 0 ? 1u : 0u);
+                    tc::mma_commit(&acc_full[b]);
+                    tc::mma_commit(&op_empty[op]);
+                    amet[b] = make_int2(op, nst);
+                    tc::mbar_arrive(&acc_full[b], 1);
+                    ++ause[b];
+                    acur ^= 1u;
+                }
+            }
+            __syncwarp();
         } else {
-            // ================= epilogue group `role` =================
+            // ================= epilogue warp =================
             const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's lanes
-            const int gbar = role == 0 ? BAR_G0 : BAR_G1;
-            int32_t* sacc = spos + NB * TN;  // column positions of the two accumulators
-            float* scr = sscr + role * 32 * kQB + qt;
-            float* bw = sbuf + role * CB * kQB + qt;
-            int32_t* bi = reinterpret_cast<int32_t*>(sbuf + NG * CB * kQB) + role * CB * kQB + qt;
+            float* scr = sscr + grp_id * 32 * kQB + qt;
+            float* bw = sbuf + grp_id * CB * kQB + qt;
+            int32_t* bi = reinterpret_cast<int32_t*>(sbuf + NG * CB * kQB) + grp_id * CB * kQB + qt;
+            if (NG == 2) acur = (uint32_t)grp_id;  // group g reads accumulator g
             // insertion threshold in w units: below the list's last key and
             // inside the error band of the current k-th key (a key above the
-            // band can never be a true k-nearest neighbour)
+            // band can never be a true k-nearest neighbour); it changes only
+            // when the list does
+            // the list's k-th entry, kept at hand: it changes only when an
+            // insertion lands before it
+            float kd = list_at(ld, kq - 1);
+            int ki = list_at(li, kq - 1);
             auto threshold = [&]() {
-                const float bnd = Bd::band(fminf(Bd::ub(list_at(ld, kq - 1), qa), qc), qa);
+                const float bnd = Bd::band(fminf(Bd::ub(kd, qa), qc), qa);
                 return __fsub_ru(fminf(ld[KC - 1], bnd), qn);
             };
-            // the BaseCase over one accumulator of nst columns (positions posv)
-            auto consume = [&](uint32_t col, int nst, const int32_t* posv) {
-                bool changed = false;
-                float t = threshold();
-                int nb = 0;
-                // candidates under the threshold are buffered per thread and
-                // inserted together by the whole warp at the end of the tile
-                auto flush = [&]() {
-                    for (int e = 0; e < nb; ++e) {
-                        const float sv = qn + bw[e * kQB];
-                        const int rp = bi[e * kQB];
-                        // (the cap pass may have listed this point already)
-                        if (key_less(sv, rp, ld[KC - 1], li[KC - 1]) && !(mono && rp == myq) &&
-                            !listed(li, rp)) {
-                            // the band moves only when the k-th key does
-                            const bool kth_moves = key_less(sv, rp, list_at(ld, kq - 1), list_at(li, kq - 1));
-                            list_insert_par(ld, li, sv, rp);
-                            t = kth_moves ? threshold() : fminf(t, __fsub_ru(ld[KC - 1], qn));
-                            changed = true;
-                            ++n_ins;
+            float t = threshold();
+            int nb = 0;
+            bool changed = false;
+            // candidates under the threshold are buffered per thread and
+            // inserted together by the whole warp at the end of the tile
+            auto flush = [&]() {
+                for (int e = 0; e < nb; ++e) {
+                    const float sv = qn + bw[e * kQB];
+                    const int rp = bi[e * kQB];
+                    // (the cap pass may have listed this point already)
+                    if (key_less(sv, rp, ld[KC - 1], li[KC - 1]) && !(mono && rp == myq) && !listed(li, rp)) {
+                        // the band moves only when the k-th key does
+                        const bool kth_moves = key_less(sv, rp, kd, ki);
+                        list_insert_par(ld, li, sv, rp);
+                        if (kth_moves) {
+                            kd = list_at(ld, kq - 1);
+                            ki = list_at(li, kq - 1);
+                            t = threshold();
+                        } else {
+                            t = fminf(t, __fsub_ru(ld[KC - 1], qn));
                         }
+                        changed = true;
+                        ++n_ins;
                     }
-                    nb = 0;
-                };
+                }
+                nb = 0;
+            };
+            // examine 32 keys from columns cb.. (rem of them belong to the tile)
+            auto examine = [&](uint32_t (&v)[32], const int2* grp, int cb, int rem) {
+                // columns past the tile's rows hold an earlier tile's values:
+                // NaN never passes a comparison and fminf ignores it
+                if (rem < 32) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (i >= rem) v[i] = 0x7fc00000u;
+                }
+                // hot path: the minimum over the 32 keys, branch-free
+                float m8[8];
+#pragma unroll
+                for (int i4 = 0; i4 < 8; ++i4)
+                    m8[i4] = fminf(fminf(__uint_as_float(v[4 * i4]), __uint_as_float(v[4 * i4 + 1])),
+                                   fminf(__uint_as_float(v[4 * i4 + 2]), __uint_as_float(v[4 * i4 + 3])));
+                const float mm = fminf(fminf(fminf(m8[0], m8[1]), fminf(m8[2], m8[3])),
+                                       fminf(fminf(m8[4], m8[5]), fminf(m8[6], m8[7])));
+                if (!(mm <= t)) return;  // per-lane control flow only: no warp collective inside
+                if (x.timers) atomicAdd(&x.timers[TT_EPI_RARE], 1ull);
+                uint32_t m = 0;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) m |= (__uint_as_float(v[i]) <= t ? 1u : 0u) << i;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) scr[i * kQB] = __uint_as_float(v[i]);
+                while (m) {
+                    const int i = __ffs(m) - 1;
+                    m &= m - 1;
+                    const float w = scr[i * kQB];
+                    if (!(w <= t)) continue;
+                    if (nb == CB) {
+                        flush();
+                        if (!(w <= t)) continue;
+                    }
+                    const int cidx = cb + i;
+                    const int2 gq = grp[cidx >> 3];
+                    const int r = cidx & 7;
+                    bw[nb * kQB] = w;
+                    bi[nb * kQB] = r < gq.y ? gq.x + r : kEmptyIdx;
+                    ++nb;
+                }
+            };
+            int since_pub = 0;
+            bool dirty = false;
+            for (;;) {
+                const int b = (int)acur;
+                long long te0 = (x.timers && warp == 0 && lane == 0) ? clock64() : 0;
+                const bool ok = tc::mbar_wait(&acc_full[b], ause[b] & 1u, x.spin_budget);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    if (lane == 0) s_fail = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                const int2 am = amet[b];
+                ++ause[b];
+                if (NG == 1) acur ^= 1u;
+                if (am.y < 0) {  // the end of the block
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&acc_empty[b], 1);
+                    break;
+                }
+                long long te1 = (x.timers && warp == 0 && lane == 0) ? clock64() : 0;
+                const int nst = am.y;
+                const int2* grp = sgrp + am.x * TN8;
+                const uint32_t tcol = tl + (uint32_t)(b * TN);
                 const int nch = (nst + 63) >> 6;
-                const uint32_t tcol = tl + col;
-                for (int cc = 0; cc < nch; ++cc) {
-                    uint32_t v[64];
-                    tc::tmem_ld64(tcol + (uint32_t)(cc * 64), v);
-                    tc::tmem_ld_wait_dep64(v);
-                    if (!act) continue;
-                    // columns past the tile's rows hold an earlier tile's values:
-                    // NaN never passes a comparison and fminf ignores it
-                    const int rem = nst - cc * 64;
-                    if (rem < 64) {
+                changed = false;
 #pragma unroll
-                        for (int i = 0; i < 64; ++i)
-                            if (i >= rem) v[i] = 0x7fc00000u;
-                    }
-                    // hot path: the minimum over the 64 columns, branch-free
-                    float m16[16];
-#pragma unroll
-                    for (int i4 = 0; i4 < 16; ++i4)
-                        m16[i4] = fminf(fminf(__uint_as_float(v[4 * i4]), __uint_as_float(v[4 * i4 + 1])),
-                                        fminf(__uint_as_float(v[4 * i4 + 2]), __uint_as_float(v[4 * i4 + 3])));
-#pragma unroll
-                    for (int hh = 8; hh > 0; hh >>= 1)
-#pragma unroll
-                        for (int i = 0; i < hh; ++i) m16[i] = fminf(m16[i], m16[i + hh]);
-                    if (!(m16[0] <= t)) continue;  // per-lane control flow only: no warp collective below
-                    if (x.timers) atomicAdd(&x.timers[TT_EPI_RARE], 1ull);
-#pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        uint32_t m = 0;
-#pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            m |= (__uint_as_float(v[32 * hh + i]) <= t ? 1u : 0u) << i;
-                        if (!m) continue;
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) scr[i * kQB] = __uint_as_float(v[32 * hh + i]);
-                        while (m) {
-                            const int i = __ffs(m) - 1;
-                            m &= m - 1;
-                            const float w = scr[i * kQB];
-                            if (!(w <= t)) continue;
-                            if (nb == CB) {
-                                flush();
-                                if (!(w <= t)) continue;
-                            }
-                            bw[nb * kQB] = w;
-                            bi[nb * kQB] = posv[cc * 64 + 32 * hh + i];
-                            ++nb;
+                for (int cc = 0; cc < TN / 64; ++cc) {
+                    if (cc < nch) {
+                        uint32_t v[64];
+                        tc::tmem_ld64_wait(tcol + (uint32_t)(cc * 64), v);
+                        if (act) {
+                            examine(*reinterpret_cast<uint32_t(*)[32]>(&v[0]), grp, cc * 64, nst - cc * 64);
+                            examine(*reinterpret_cast<uint32_t(*)[32]>(&v[32]), grp, cc * 64 + 32,
+                                    nst - cc * 64 - 32);
                         }
                     }
+                }
+                // every lane's TMEM reads are done and its candidates' points
+                // are resolved: the accumulator and the slot go back
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) {
+                    tc::mbar_arrive(&acc_empty[b], 1);
+                    tc::mbar_arrive(&op_empty[am.x], 1);
                 }
                 // the whole warp inserts its buffered candidates together
-                const int mx = __reduce_max_sync(0xffffffffu, nb);
-                if (mx > 0) flush();
-                return changed;
-            };
-            // publish this warp's bounds after a tile changed a list
-            auto publish = [&](bool changed) {
-                if (!__any_sync(0xffffffffu, changed)) return;  // the published bound stands
-                float ub = fminf(Bd::ub(list_at(ld, kq - 1), qa), qc);
-                float vmax = act ? ub : -INFINITY, vmin = act ? ub : INFINITY;
+                if (__reduce_max_sync(0xffffffffu, nb) > 0) flush();
+                // publish this warp's bounds for the planner's next window (a
+                // later publication only prunes later; any is valid)
+                dirty |= __any_sync(0xffffffffu, changed);
+                if (dirty && ++since_pub >= 4) {
+                    float ub = fminf(Bd::ub(kd, qa), qc);
+                    float vmax = act ? ub : -INFINITY, vmin = act ? ub : INFINITY;
 #pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
-                    vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, off));
+                    for (int off = 16; off > 0; off >>= 1) {
+                        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
+                        vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, off));
+                    }
+                    if (lane == 0) {
+                        s_wmax[warp] = vmax;
+                        s_wmin[warp] = vmin;
+                    }
+                    dirty = false;
+                    since_pub = 0;
                 }
-                if (lane == 0) {
-                    s_wmax[warp] = vmax;
-                    s_wmin[warp] = vmin;
-                }
-            };
-            // issue the MMAs of slot op into accumulator acc (group leader only)
-            auto issue = [&](int op, int acc) {
-                const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB + op * TN * S::RB);
-#pragma unroll
-                for (int m = 0; m < S::NK; ++m)
-                    tc::mma<TcFmt<FMT>::hw>(tmem + (uint32_t)(acc * TN),
-                                            tc::sdesc(a0 + 256u * S::astep(m), 128u, S::GB),
-                                            tc::sdesc(b0 + 256u * S::bstep(m), 128u, S::GB), idesc,
-                                            m > 0 ? 1u : 0u);
-                tc::mma_commit(&acc_full[acc]);
-                tc::mma_commit(&op_empty[op]);
-            };
-            if constexpr (NG == 2) {
-                for (;;) {
-                    // this group's next tile: operand slot op (or an end marker)
-                    const int op = (int)(ctile % NB);
-                    const uint32_t ouse = ctile / NB;
-                    long long te0 = clock64();
-                    bool ok = tc::mbar_wait(&op_full[op], ouse & 1u, x.spin_budget);
-                    if (!__all_sync(0xffffffffu, ok) && lane == 0) s_gfail[role] = 1;
-                    const int nst = ok ? ometa[op] : -1;
-                    // every warp of the group is done with the last tile (its TMEM
-                    // reads and its column positions) before either is replaced
-                    tc::fence_before_sync();
-                    tc::named_sync(gbar, 128);
-                    tc::fence_after_sync();
-                    long long te1 = clock64();
-                    if (s_gfail[role]) {
-                        s_fail = 1;
-                        break;
-                    }
-                    ctile += 2;
-                    if (nst < 0) {
-                        if (qt == 0) tc::mbar_arrive(&op_empty[op], 2);  // nothing reads the slot
-                        break;
-                    }
-                    if (qt == 0) issue(op, role);
-                    ++issued;
-                    // the slot's column positions move to the accumulator's, so the
-                    // slot can be refilled while this group works
-                    for (int i = qt; i < TN; i += kQB) sacc[role * TN + i] = spos[op * TN + i];
-                    ok = tc::mbar_wait(&acc_full[role], par_of(done), x.spin_budget);
-                    if (!__all_sync(0xffffffffu, ok) && lane == 0) s_gfail[role] = 1;
-                    tc::named_sync(gbar, 128);  // also: every position is copied
-                    if (s_gfail[role]) {
-                        s_fail = 1;
-                        break;
-                    }
-                    ++done;
-                    if (qt == 0) tc::mbar_arrive(&op_empty[op], 1);
-                    tc::fence_after_sync();
-                    long long te2 = clock64();
-                    const bool changed = consume((uint32_t)(role * TN), nst, sacc + role * TN);
-                    publish(changed);
-                    if (x.timers && (warp & 3) == 0 && lane == 0) {
-                        atomicAdd(&x.timers[TT_EPI_WAIT_OP], (unsigned long long)(te1 - te0));
-                        atomicAdd(&x.timers[TT_EPI_WAIT_ACC], (unsigned long long)(te2 - te1));
-                        atomicAdd(&x.timers[TT_EPI_WORK], (unsigned long long)(clock64() - te2));
-                    }
-                }
-            } else {
-                // one group, two accumulators: the MMA of tile j + 1 is issued
-                // before tile j is read
-                int nstq[2] = {0, 0};
-                bool ended = false;
-                for (;;) {
-                    if (!ended && issued - done < 2) {
-                        const int op = (int)(ctile % NB);
-                        const uint32_t ouse = ctile / NB;
-                        long long te0 = clock64();
-                        bool ok = tc::mbar_wait(&op_full[op], ouse & 1u, x.spin_budget);
-                        if (!__all_sync(0xffffffffu, ok) && lane == 0) s_gfail[0] = 1;
-                        const int nst = ok ? ometa[op] : -1;
-                        // every warp is done with the accumulator (and positions)
-                        // this tile replaces: the tile read before the last one
-                        tc::fence_before_sync();
-                        tc::named_sync(BAR_G0, 128);
-                        tc::fence_after_sync();
-                        if (x.timers && (warp & 3) == 0 && lane == 0)
-                            atomicAdd(&x.timers[TT_EPI_WAIT_OP], (unsigned long long)(clock64() - te0));
-                        if (s_gfail[0]) {
-                            s_fail = 1;
-                            break;
-                        }
-                        ++ctile;
-                        if (nst < 0) {
-                            if (qt == 0) tc::mbar_arrive(&op_empty[op], 2);
-                            ended = true;
-                            continue;
-                        }
-                        const int acc = (int)(issued & 1u);
-                        if (qt == 0) issue(op, acc);
-                        for (int i = qt; i < TN; i += kQB) sacc[acc * TN + i] = spos[op * TN + i];
-                        nstq[acc] = nst;
-                        ++issued;
-                        tc::named_sync(BAR_G0, 128);  // every position is copied
-                        if (qt == 0) tc::mbar_arrive(&op_empty[op], 1);
-                        continue;
-                    }
-                    if (done == issued) break;  // the end marker came and every tile is read
-                    const int acc = (int)(done & 1u);
-                    long long te1 = clock64();
-                    bool ok = tc::mbar_wait(&acc_full[acc], par_of(done), x.spin_budget);
-                    if (!__all_sync(0xffffffffu, ok) && lane == 0) s_gfail[0] = 1;
-                    tc::named_sync(BAR_G0, 128);
-                    if (s_gfail[0]) {
-                        s_fail = 1;
-                        break;
-                    }
-                    ++done;
-                    tc::fence_after_sync();
-                    long long te2 = clock64();
-                    const bool changed = consume((uint32_t)(acc * TN), acc ? nstq[1] : nstq[0], sacc + acc * TN);
-                    publish(changed);
-                    if (x.timers && (warp & 3) == 0 && lane == 0) {
-                        atomicAdd(&x.timers[TT_EPI_WAIT_ACC], (unsigned long long)(te2 - te1));
-                        atomicAdd(&x.timers[TT_EPI_WORK], (unsigned long long)(clock64() - te2));
-                    }
+                if (x.timers && warp == 0 && lane == 0) {
+                    atomicAdd(&x.timers[TT_EPI_WAIT], (unsigned long long)(te1 - te0));
+                    atomicAdd(&x.timers[TT_EPI_WORK], (unsigned long long)(clock64() - te1));
                 }
             }
         }
         // every role is done with the item or gave up; a failed item writes
         // nothing (its lists may be incomplete, and copies may still land in
-        // the buffers the merge and re-rank would reuse)
+        // the buffers the re-rank would reuse)
         __syncthreads();
         if (s_fail) break;
-        if (role < 2) {
-            long long tf0 = clock64();
-            if constexpr (NG == 2) {
-                // merge group 1's lists into group 0's
-                float* smd = reinterpret_cast<float*>(smem);
-                int32_t* smi = reinterpret_cast<int32_t*>(smem + kQB * KC * 4);
-                if (role == 1) {
+        if (epi && NG == 2) {
+            // merge group 1's lists into group 0's
+            float* smd = reinterpret_cast<float*>(smem);
+            int32_t* smi = reinterpret_cast<int32_t*>(smem + kQB * KC * 4);
+            if (grp_id == 1) {
 #pragma unroll
-                    for (int j = 0; j < KC; ++j) {
-                        smd[j * kQB + qt] = ld[j];
-                        smi[j * kQB + qt] = li[j];
-                    }
-                }
-                tc::named_sync(BAR_EPI, 256);
-                if (role == 0) {
-#pragma unroll
-                    for (int j = 0; j < KC; ++j) {
-                        const float d = smd[j * kQB + qt];
-                        const int i = smi[j * kQB + qt];
-                        if (!listed(li, i) && key_less(d, i, ld[KC - 1], li[KC - 1])) list_insert(ld, li, d, i);
-                    }
-                    // the re-rank below reuses the merge buffers: all of group 0 has read them
-                    tc::named_sync(BAR_G0, 128);
+                for (int j = 0; j < KC; ++j) {
+                    smd[j * kQB + qt] = ld[j];
+                    smi[j * kQB + qt] = li[j];
                 }
             }
-            if (role == 0) {
-                // ---- finish the work item
-                const float ubk = fminf(Bd::ub(list_at(ld, kq - 1), qa), qc);
-                const float band = Bd::band(ubk, qa);
-                const bool ovf = act && li[KC - 1] != kEmptyIdx && !(ld[KC - 1] > band);
-                if (ovf) {
-                    a.fbq_list[atomicAdd(a.fbq_count, 1)] = make_int4(myq, blk, __float_as_int(ubk), 0);
-                } else if (act) {
-                    // float64 re-rank of the band candidates in shared memory
-                    double* rd = reinterpret_cast<double*>(smem);
-                    int32_t* ri = reinterpret_cast<int32_t*>(smem + kQB * KC * 8);
-                    const float* qp = P.qpts + (int64_t)myq * DP;
-                    int nb = 0;
+            tc::named_sync(1, 256);
+            if (grp_id == 0) {
 #pragma unroll
-                    for (int j = 0; j < KC; ++j) {
-                        if (li[j] != kEmptyIdx && !(ld[j] > band)) {
-                            rd[nb * kQB + qt] = exact_d2<DP>(qp, P.rpts + (int64_t)li[j] * DP);
-                            ri[nb * kQB + qt] = P.ridx[li[j]];
-                            ++nb;
-                        }
-                    }
-                    n_re += nb;
-                    const int64_t base = (int64_t)P.qidx[myq] * kq;
-                    for (int j = 0; j < kq; ++j) {
-                        int best = j;
-                        for (int c = j + 1; c < nb; ++c)
-                            if (key_less(rd[c * kQB + qt], ri[c * kQB + qt], rd[best * kQB + qt], ri[best * kQB + qt]))
-                                best = c;
-                        const double bd = rd[best * kQB + qt];
-                        const int bix = ri[best * kQB + qt];
-                        rd[best * kQB + qt] = rd[j * kQB + qt];
-                        ri[best * kQB + qt] = ri[j * kQB + qt];
-                        P.out_idx[base + j] = bix;
-                        P.out_dist[base + j] = (float)sqrt(bd);
+                for (int j = 0; j < KC; ++j) {
+                    const float d = smd[j * kQB + qt];
+                    const int i = smi[j * kQB + qt];
+                    if (!listed(li, i) && key_less(d, i, ld[KC - 1], li[KC - 1])) list_insert(ld, li, d, i);
+                }
+            }
+            // the re-rank below reuses the merge buffers: group 0 has read them
+            tc::named_sync(1, 256);
+        }
+        if (epi && grp_id == 0) {
+            // ---- finish the work item
+            long long tf0 = x.timers ? clock64() : 0;
+            const float ubk = fminf(Bd::ub(list_at(ld, kq - 1), qa), qc);
+            const float band = Bd::band(ubk, qa);
+            const bool ovf = act && li[KC - 1] != kEmptyIdx && !(ld[KC - 1] > band);
+            if (ovf) {
+                a.fbq_list[atomicAdd(a.fbq_count, 1)] = make_int4(myq, blk, __float_as_int(ubk), 0);
+            } else if (act) {
+                // float64 re-rank of the band candidates in shared memory
+                double* rd = reinterpret_cast<double*>(smem);
+                int32_t* ri = reinterpret_cast<int32_t*>(smem + kQB * KC * 8);
+                const float* qp = P.qpts + (int64_t)myq * DP;
+                int nr = 0;
+#pragma unroll
+                for (int j = 0; j < KC; ++j) {
+                    if (li[j] != kEmptyIdx && !(ld[j] > band)) {
+                        rd[nr * kQB + qt] = exact_d2<DP>(qp, P.rpts + (int64_t)li[j] * DP);
+                        ri[nr * kQB + qt] = P.ridx[li[j]];
+                        ++nr;
                     }
                 }
-                if (x.timers && qt == 0)
-                    atomicAdd(&x.timers[TT_EPI_FINISH], (unsigned long long)(clock64() - tf0));
+                n_re += nr;
+                const int64_t base = (int64_t)P.qidx[myq] * kq;
+                for (int j = 0; j < kq; ++j) {
+                    int best = j;
+                    for (int c = j + 1; c < nr; ++c)
+                        if (key_less(rd[c * kQB + qt], ri[c * kQB + qt], rd[best * kQB + qt], ri[best * kQB + qt]))
+                            best = c;
+                    const double bd = rd[best * kQB + qt];
+                    const int bix = ri[best * kQB + qt];
+                    rd[best * kQB + qt] = rd[j * kQB + qt];
+                    ri[best * kQB + qt] = ri[j * kQB + qt];
+                    P.out_idx[base + j] = bix;
+                    P.out_dist[base + j] = (float)sqrt(bd);
+                }
             }
+            if (x.timers && qt == 0)
+                atomicAdd(&x.timers[TT_EPI_FINISH], (unsigned long long)(clock64() - tf0));
         }
         __syncthreads();
     }
     if (s_fail) {
         // drain this CTA's own asynchronous work before TMEM and shared
         // memory are released: the planner's last NB slot fills (their bulk
-        // copies) and each group's MMAs whose accumulator was not read
+        // copies) and the issuer's MMAs
         if (warp == PW && lane == 0) {
             const uint32_t i0 = otile > (uint32_t)NB ? otile - NB : 0u;
             for (uint32_t i = i0; i < otile; ++i) tc::mbar_wait(&op_full[i % NB], (i / NB) & 1u, kDrainPolls);
         }
-        if (role < 2 && qt == 0)
-            for (uint32_t j = done; j < issued; ++j) tc::mbar_wait(&acc_full[acc_of(j)], par_of(j), kDrainPolls);
+        if (warp == MW && lane == 0)
+            for (int b = 0; b < 2; ++b)
+                if (ause[b] > 0) tc::mbar_wait(&acc_full[b], (ause[b] - 1) & 1u, kDrainPolls);
         if (tid == 0) atomicExch(x.err, 1);
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == PW) tc::tmem_dealloc(tmem, 2 * TN);
+    if (warp == MW) tc::tmem_dealloc(tmem, 2 * TN);
     if (n_skip) atomicAdd(&a.stats[ST_SKIPPED], n_skip);
     if (n_eval) atomicAdd(&a.stats[ST_EVALUATED], n_eval);
     if (n_pp) atomicAdd(&a.stats[ST_POINT_PAIRS], n_pp);
@@ -1020,8 +983,9 @@ template <int DP>
 int launch_tile_tc(const TileArgs& a, int fmt, int kc, int items, int* err, int spin, cudaStream_t s) {
     TcExtra x{err, spin, g_tc_timers, g_tc_stall};
     const int F = tc_format(fmt);
-    // two epilogue groups where their lists and scratch fit, else one group
-    // with two accumulators
+    // two epilogue groups where their lists leave room for a second group's
+    // registers (ten warps put three on a sub-partition: 168 registers a
+    // thread) and their scratch fits shared memory; else one group
 #define DT_TC_CASE(FMTV, KCV)                                                              \
     if (F == FMTV && kc == KCV) {                                                          \
         constexpr int NGV = (KCV <= 32 && DP <= 32) ? 2 : 1;                               \
@@ -1029,9 +993,10 @@ int launch_tile_tc(const TileArgs& a, int fmt, int kc, int items, int* err, int 
         size_t smem = tc_smem_bytes<FMTV, DP, KCV, NGV>();                                 \
         DT_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                       (int)smem));                                         \
-        int g = occupancy_grid((const void*)kern, NGV * 128 + 32, smem);                   \
+        const int nt = 32 * (4 * NGV + 2);                                                 \
+        int g = occupancy_grid((const void*)kern, nt, smem);                               \
         if (items < g) g = items > 0 ? items : 1;                                          \
-        DT_LAUNCH(kern, g, NGV * 128 + 32, smem, s, a, x);                                 \
+        DT_LAUNCH(kern, g, nt, smem, s, a, x);                                             \
         return DTREE_OK;                                                                   \
     }
     DT_TC_CASE(2, 16)

@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
             };
             refresh_bound();
 
-            const int nseed = MODE == MODE_MAIN ? 0 : seed_count(a.seed_nleaf, a.seed_slots, blk);
+            const int nseed = MODE == MODE_MAIN ? 0 : seed_count_n(a.seed_nleaf, a.seed_slots, a.seed_eval_slots, blk);
             const int64_t c0 = MODE == MODE_SEED ? 0 : a.csr_off[blk];
             const int64_t c1 = MODE == MODE_SEED ? 0 : a.csr_off[blk + 1];
             const int64_t ntot = nseed + (c1 - c0);

@@ -150,3 +150,4 @@ extern "C" int dtree_debug_tc_stall(int32_t on) {
     dt::g_tc_stall = on ? 1 : 0;
     return DTREE_OK;
 }
+

@@ -524,9 +524,8 @@ def dtree_debug_mma(A: torch.Tensor, B: torch.Tensor, fmt: str = "bf16", stream=
     return out
 
 
-TC_TIMERS = ("plan_window", "plan_wait", "plan_stage", "epi_wait_op", "epi_wait_acc",
-             "epi_work", "epi_rare_chunks", "epi_finish", "item_setup", "tiles", "items",
-             "inserts")
+TC_TIMERS = ("plan_window", "plan_wait", "plan_stage", "mma_wait", "epi_wait", "epi_work",
+             "epi_rare_chunks", "epi_finish", "item_setup", "tiles", "items", "inserts")
 
 
 def dtree_debug_tc_stall(on: bool) -> None:

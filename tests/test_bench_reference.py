@@ -15,6 +15,7 @@ KEYS = {"impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_
 @pytest.mark.parametrize("op,extra", [("knn", ["--ref-queries", "8"]),
                                       ("knn", ["--workload", "latent3", "--ref-queries", "8"]),
                                       ("knn", ["--workload", "gmm16"]),
+                                      ("knn", ["--workload", "batched", "--ref-queries", "16"]),
                                       ("kfn", []), ("range", []), ("emst", [])])
 def test_reference_arm_prints_one_line(op, extra):
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--op", op,

@@ -144,3 +144,44 @@ def test_model_save_load_round_trip(dt, tmp_path):
     finally:
         for t in (tr, tq, tt, tr2, other):
             t.free()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_proposal_with_tensor_cores_is_exact(dt, prec):
+    # the tensor-core search evaluates the proposed cells first in its main
+    # pass; the lists, and so the results, are those of the search without it
+    W, tr, tq, tt = _setup(dt, 200_000, 20_000, 20_000)
+    try:
+        model = dt.dtree_proposal_train(tr, tt, W.k, epochs=5, batch=128)
+        dt.dtree_attach_proposal(tr, model)
+        base = dt.dtree_knn(tq, tr, W.k, precision=prec)
+        ti, td = truth(W.ref, W.query, W.k)
+        compare(base[0].cpu().numpy(), base[1].cpu().numpy(), ti, td, W.k)
+        for M in (1, 4, 8):
+            idx, dist, st = dt.dtree_knn(tq, tr, W.k, precision=prec, proposal=M, with_stats=True)
+            assert torch.equal(idx, base[0]) and torch.equal(dist, base[1]), M
+        dt.dtree_attach_proposal(tr, None)
+        model.free()
+    finally:
+        for t in (tr, tq, tt):
+            t.free()
+
+
+def test_proposal_with_tensor_cores_at_k50_d64(dt):
+    W = inputs.powerlaw64(n_ref=60_000, n_query=6_000, n_train=6_000)
+    tr = dt.dtree_build(torch.from_numpy(W.ref).cuda(), 32)
+    tq = dt.dtree_build(torch.from_numpy(W.query).cuda(), 32)
+    tt = dt.dtree_build(torch.from_numpy(W.extra["train"]).cuda(), 32)
+    try:
+        model = dt.dtree_proposal_train(tr, tt, W.k, epochs=5, batch=64, seed_points=256)
+        dt.dtree_attach_proposal(tr, model)
+        base = dt.dtree_knn(tq, tr, W.k, precision="bf16")
+        idx, dist = dt.dtree_knn(tq, tr, W.k, precision="bf16", proposal=4)
+        assert torch.equal(idx, base[0]) and torch.equal(dist, base[1])
+        ti, td = truth(W.ref, W.query, W.k)
+        compare(idx.cpu().numpy(), dist.cpu().numpy(), ti, td, W.k)
+        dt.dtree_attach_proposal(tr, None)
+        model.free()
+    finally:
+        for t in (tr, tq, tt):
+            t.free()
