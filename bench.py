@@ -261,7 +261,7 @@ WORKLOADS = {
                  "Gaussian with power-law covariance spectrum (eigenvalue i ~ i^-1.5, random rotation)"),
         "make": lambda a, rank: inputs.powerlaw64(n_ref=a.n_ref or 2_000_000, n_query=a.n_query or 2_000_000,
                                                   n_train=a.train_queries, shard=rank),
-        "precision": "bf16", "proposal": 4, "cpu_queries": 256,
+        "precision": "bf16", "proposal": 1, "cpu_queries": 256,
     },
     # the learned-proposal configuration at d = 8
     "latent3": {

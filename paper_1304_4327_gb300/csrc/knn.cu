@@ -222,14 +222,17 @@ __global__ void __launch_bounds__(256) k_expand(const ProbDev* __restrict__ prob
             }
             be = __shfl_sync(0xffffffffu, be, 0) + __popc(me & lt);
             bf = __shfl_sync(0xffffffffu, bf, 0) + __popc(mf & lt);
-            if (do_emit) {
-                if (be < capp) {
-                    outp[be] = e4;
-                    atomicAdd(&bcount[e4.x], 1);
-                    ++em;
-                } else {
-                    *overflow = 1;
-                }
+            const bool stored = do_emit && be < capp;
+            const unsigned ms = __ballot_sync(0xffffffffu, stored);
+            if (stored) {
+                outp[be] = e4;
+                ++em;
+                // the block's count, one atomic per distinct block among the
+                // warp's lanes (a frontier's pairs come grouped by query node)
+                const unsigned peers = __match_any_sync(ms, e4.x);
+                if (lane == __ffs(peers) - 1) atomicAdd(&bcount[e4.x], __popc(peers));
+            } else if (do_emit) {
+                *overflow = 1;
             }
             if (do_push) {
                 if (bf < cap) fout[bf] = f2;
