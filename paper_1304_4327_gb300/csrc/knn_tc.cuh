@@ -798,19 +798,15 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                 const int nst = am.y;
                 const int2* grp = sgrp + am.x * TN8;
                 const uint32_t tcol = tl + (uint32_t)(b * TN);
-                const int nch = (nst + 63) >> 6;
+                const int nch = (nst + 31) >> 5;
                 changed = false;
-#pragma unroll
-                for (int cc = 0; cc < TN / 64; ++cc) {
-                    if (cc < nch) {
-                        uint32_t v[64];
-                        tc::tmem_ld64_wait(tcol + (uint32_t)(cc * 64), v);
-                        if (act) {
-                            examine(*reinterpret_cast<uint32_t(*)[32]>(&v[0]), grp, cc * 64, nst - cc * 64);
-                            examine(*reinterpret_cast<uint32_t(*)[32]>(&v[32]), grp, cc * 64 + 32,
-                                    nst - cc * 64 - 32);
-                        }
-                    }
+                // a loop, not unrolled: one copy of the examine path keeps the
+                // kernel's code within the instruction cache
+#pragma unroll 1
+                for (int cc = 0; cc < nch; ++cc) {
+                    uint32_t v[32];
+                    tc::tmem_ld32_wait(tcol + (uint32_t)(cc * 32), v);
+                    if (act) examine(v, grp, cc * 32, nst - cc * 32);
                 }
                 // every lane's TMEM reads are done and its candidates' points
                 // are resolved: the accumulator and the slot go back
