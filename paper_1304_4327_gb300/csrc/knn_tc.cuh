@@ -106,12 +106,13 @@ template <int FMT, int DP, int KC, int NG>
 struct TcSmem {
     using S = TcShape<FMT, DP>;
     static constexpr int NB = 4;                                     // operand slots
+    static constexpr int GR = 8;                                     // row-group tables (a ring)
     static constexpr int WIN = 256;                                  // candidates per window
     static constexpr int CB = 8;                                     // deferred insertions per thread
     static constexpr int OFF_A = 0;                                  // 128 x RB
     static constexpr int OFF_B = OFF_A + kQB * S::RB;                // NB x TN x RB
-    static constexpr int OFF_GRP = OFF_B + NB * S::TN * S::RB;       // NB x TN8 int2 (row groups)
-    static constexpr int OFF_WIN = OFF_GRP + NB * S::TN8 * 8;        // 2 x WIN (leaf int, d_min float)
+    static constexpr int OFF_GRP = OFF_B + NB * S::TN * S::RB;       // GR x TN8 int2 (row groups)
+    static constexpr int OFF_WIN = OFF_GRP + GR * S::TN8 * 8;        // 2 x WIN (leaf int, d_min float)
     static constexpr int OFF_WENT = OFF_WIN + 2 * WIN * 8;           // WIN int4 (begin, count, leaf, group0)
     static constexpr int OFF_SCR = OFF_WENT + WIN * 16;              // NG x 32 x 128 float
     static constexpr int OFF_BUF = OFF_SCR + NG * 32 * kQB * 4;      // NG x CB x 128 (float, int)
@@ -284,6 +285,11 @@ struct TcExtra {
 // is fixed and far above their duration, independent of the caller's
 // spin_budget.
 constexpr int kDrainPolls = 1 << 22;
+// End-of-tile insertion policy of the tile kernel's epilogue warps: insert
+// when at least kFlushLanes lanes hold buffered candidates, or after
+// kFlushTiles tiles with some pending.
+constexpr int kFlushLanes = 8;
+constexpr int kFlushTiles = 16;
 
 // Diagnostic cycle counters of the tile kernel (summed over CTAs; read only
 // when timers are attached).
@@ -300,6 +306,11 @@ enum TcTimer {
     TT_TILES,            // planner: tiles produced
     TT_ITEMS,            // items processed
     TT_INSERTS,          // epilogue (all threads): candidate-list insertions
+    TT_EPI_LD,           // epilogue (warp 0): TMEM reads, issue to completion
+    TT_RED_MISMATCH,     // epilogue (all threads): load-reduced minima unlike the computed ones
+    TT_EPI_LOOP,         // epilogue (warp 0): the column loop (reads, thresholds, buffering)
+    TT_EPI_FLUSH,        // epilogue (warp 0): the release and the end-of-tile insertions
+    TT_MMA_WAIT_ACC,     // MMA warp: the part of TT_MMA_WAIT spent waiting for an accumulator
     TT_N
 };
 static_assert(TT_N <= 32, "the diagnostic timer buffer holds 32 counters");
@@ -308,8 +319,8 @@ static_assert(TT_N <= 32, "the diagnostic timer buffer holds 32 counters");
 //   warps 0 .. 4 NG - 1  NG epilogue groups of four warps: one query row (TMEM
 //              lane) per thread; each warp reads its own 32 lanes of an
 //              accumulator, examines the keys and keeps its queries' lists,
-//              and hands the accumulator and the operand slot back by mbarrier
-//              arrivals, independently of the other warps.  Tiles alternate
+//              and hands the accumulator and the tile's row-group table back
+//              by mbarrier arrivals, independently of the other warps.  Tiles alternate
 //              between two accumulators: with NG = 1 the group reads both in
 //              turn; with NG = 2 group g reads accumulator g and keeps its own
 //              lists, which are merged when the block is done
@@ -317,14 +328,17 @@ static_assert(TT_N <= 32, "the diagnostic timer buffer holds 32 counters");
 //              a time (Algorithm 3's test against the block's bound, each
 //              kept leaf's range and its place in the window's run of 8-row
 //              groups), then fills operand slots with whole 8-row groups by
-//              bulk copies (TMA) of the leaves' operand rows
+//              bulk copies (TMA) of the leaves' operand rows, and a table of
+//              the groups' first rows (a ring of GR tables, deeper than the
+//              slots: a slot is free again once its MMAs are done)
 //   warp 4 NG + 1  MMA issuer: one thread turns a filled slot into an
 //              accumulator (two in turn) with tcgen05.mma
 // Hand-over by mbarriers: op_full (planner -> MMA: its arrival plus the
 // copied bytes), acc_full (MMA -> epilogue: the MMA's commit plus the
 // issuer's arrival with the tile's slot and columns), acc_empty (epilogue ->
 // MMA: one arrival per warp once its lanes are read), op_empty (MMA commit
-// and the four epilogue warps -> planner).  Every wait is bounded; after a
+// -> planner), gr_empty (the four epilogue warps -> planner: the tile's
+// row-group table is read).  Every wait is bounded; after a
 // failed wait the item's work is abandoned, the kernel drains its own copies
 // and MMAs, releases TMEM and reports through x.err.
 template <int FMT, int DP, int KC, int NG>
@@ -332,21 +346,21 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
     using S = TcShape<FMT, DP>;
     using L = TcSmem<FMT, DP, KC, NG>;
     using Bd = TcBound<FMT, DP>;
-    constexpr int TN = S::TN, TN8 = S::TN8, NB = L::NB, CB = L::CB, WIN = L::WIN;
+    constexpr int TN = S::TN, TN8 = S::TN8, NB = L::NB, GR = L::GR, CB = L::CB, WIN = L::WIN;
     constexpr int PW = 4 * NG, MW = 4 * NG + 1;  // the planner's and the MMA issuer's warps
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem + L::OFF_A;
     unsigned char* sB = smem + L::OFF_B;
-    int2* sgrp = reinterpret_cast<int2*>(smem + L::OFF_GRP);   // NB x TN8
+    int2* sgrp = reinterpret_cast<int2*>(smem + L::OFF_GRP);   // GR x TN8
     int32_t* swleaf = reinterpret_cast<int32_t*>(smem + L::OFF_WIN);
     float* swdmin = reinterpret_cast<float*>(smem + L::OFF_WIN + 2 * WIN * 4);
     int4* went = reinterpret_cast<int4*>(smem + L::OFF_WENT);
     float* sscr = reinterpret_cast<float*>(smem + L::OFF_SCR);
     float* sbuf = reinterpret_cast<float*>(smem + L::OFF_BUF);
     float* scen = reinterpret_cast<float*>(smem + L::OFF_CEN);
-    __shared__ uint64_t op_full[NB], op_empty[NB], acc_full[2], acc_empty[2], never;
+    __shared__ uint64_t op_full[NB], op_empty[NB], gr_empty[GR], acc_full[2], acc_empty[2], never;
     __shared__ int ometa[NB];
-    __shared__ int2 amet[2];  // the tile in each accumulator: (slot, columns), columns < 0 ends the block
+    __shared__ int2 amet[2];  // the tile in each accumulator: (table, columns), columns < 0 ends the block
     __shared__ uint32_t s_tmem;
     __shared__ int s_item;
     __shared__ ProbDev s_prob;
@@ -363,8 +377,9 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
     if (tid == 0) {
         for (int i = 0; i < NB; ++i) {
             tc::mbar_init(&op_full[i], 1);   // the planner's arrival (+ copied bytes)
-            tc::mbar_init(&op_empty[i], 5);  // tcgen05.commit + the four epilogue warps
+            tc::mbar_init(&op_empty[i], 1);  // tcgen05.commit
         }
+        for (int i = 0; i < GR; ++i) tc::mbar_init(&gr_empty[i], 4);  // the four epilogue warps
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(&acc_full[i], 2);   // tcgen05.commit + the issuer's arrival
             tc::mbar_init(&acc_empty[i], 4);  // the four epilogue warps
@@ -381,7 +396,11 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
     const uint32_t idesc = tc::idesc(TcFmt<FMT>::hw, kQB, TN);
     // the barriers' phases carry over from item to item, so the counters do too
     uint32_t otile = 0;                  // planner / MMA issuer: operand slot uses
-    uint32_t ause[2] = {0u, 0u};         // MMA issuer / each epilogue warp: uses of each accumulator
+    uint32_t gtile = 0;                  // planner / MMA issuer: tiles (row-group table uses)
+    // MMA issuer / each epilogue warp: bit b of aph is the parity of the uses
+    // of accumulator b, bit b of aused whether it was used (bit masks, not an
+    // array: a dynamically indexed array would live in local memory)
+    uint32_t aph = 0u, aused = 0u;
     uint32_t acur = 0;                   // MMA issuer / each epilogue warp: the next accumulator
 
     const ProbDev& P = s_prob;
@@ -560,7 +579,11 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                     const int op = (int)(otile % NB);
                     const uint32_t use = otile / NB;
                     long long t1 = x.timers ? clock64() : 0;
-                    const bool ok = lane == 0 ? tc::mbar_wait(&op_empty[op], (use & 1u) ^ 1u, x.spin_budget) : true;
+                    const int gi = (int)(gtile % GR);
+                    const uint32_t guse = gtile / GR;
+                    const bool ok = lane == 0 ? tc::mbar_wait(&op_empty[op], (use & 1u) ^ 1u, x.spin_budget) &&
+                                                    tc::mbar_wait(&gr_empty[gi], (guse & 1u) ^ 1u, x.spin_budget)
+                                              : true;
                     if (!__all_sync(0xffffffffu, ok)) {
                         fail = true;
                         break;
@@ -569,7 +592,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                     if (lane == 0) tc::mbar_expect_tx(&op_full[op], (uint32_t)(g1 - g0) * S::GB);
                     __syncwarp();
                     unsigned char* slot = sB + op * TN * S::RB;
-                    int2* grp = sgrp + op * TN8;
+                    int2* grp = sgrp + gi * TN8;
                     for (;;) {
                         const int i = cur + lane;
                         const bool valid = i < wn;
@@ -606,6 +629,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                         }
                     }
                     ++otile;
+                    ++gtile;
                 }
             }
             // a window fetch still in flight (after a failure) lands before the
@@ -650,15 +674,16 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                     if (nst < 0) {
                         // the end of the block: nothing reads the slot; the
                         // accumulators carry the marker to each epilogue group
-                        tc::mbar_arrive(&op_empty[op], 5);
+                        tc::mbar_arrive(&op_empty[op], 1);
                         bool ok = true;
                         for (int e = 0; e < NG && ok; ++e) {
                             const int b = (int)acur;
-                            ok = tc::mbar_wait(&acc_empty[b], (ause[b] & 1u) ^ 1u, x.spin_budget);
+                            ok = tc::mbar_wait(&acc_empty[b], ((aph >> b) & 1u) ^ 1u, x.spin_budget);
                             if (ok) {
                                 amet[b] = make_int2(op, -1);
                                 tc::mbar_arrive(&acc_full[b], 2);
-                                ++ause[b];
+                                aph ^= 1u << b;
+                                aused |= 1u << b;
                                 acur ^= 1u;
                             }
                         }
@@ -666,11 +691,16 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                         break;
                     }
                     const int b = (int)acur;
-                    if (!tc::mbar_wait(&acc_empty[b], (ause[b] & 1u) ^ 1u, x.spin_budget)) {
+                    const long long ta = x.timers ? clock64() : 0;
+                    if (!tc::mbar_wait(&acc_empty[b], ((aph >> b) & 1u) ^ 1u, x.spin_budget)) {
                         s_fail = 1;
                         break;
                     }
-                    if (x.timers) atomicAdd(&x.timers[TT_MMA_WAIT], (unsigned long long)(clock64() - t0));
+                    if (x.timers) {
+                        const long long tb = clock64();
+                        atomicAdd(&x.timers[TT_MMA_WAIT], (unsigned long long)(tb - t0));
+                        atomicAdd(&x.timers[TT_MMA_WAIT_ACC], (unsigned long long)(tb - ta));
+                    }
                     tc::fence_after_sync();
                     const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB + op * TN * S::RB);
 #pragma unroll
@@ -680,10 +710,12 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                                                 tc::sdesc(b0 + 256u * S::bstep(m), 128u, S::GB), idesc,
                                                 m > 0 ? 1u : 0u);
                     tc::mma_commit(&acc_full[b]);
-                    tc::mma_commit(&op_empty[op]);
-                    amet[b] = make_int2(op, nst);
+                    tc::mma_commit(&op_empty[op]);  // the slot is free once the MMAs are done
+                    amet[b] = make_int2((int)(gtile % GR), nst);
+                    ++gtile;
                     tc::mbar_arrive(&acc_full[b], 1);
-                    ++ause[b];
+                    aph ^= 1u << b;
+                    aused |= 1u << b;
                     acur ^= 1u;
                 }
             }
@@ -734,23 +766,28 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                 }
                 nb = 0;
             };
-            // examine 32 keys from columns cb.. (rem of them belong to the tile)
-            auto examine = [&](uint32_t (&v)[32], const int2* grp, int cb, int rem) {
-                // columns past the tile's rows hold an earlier tile's values:
-                // NaN never passes a comparison and fminf ignores it
-                if (rem < 32) {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        if (i >= rem) v[i] = 0x7fc00000u;
-                }
-                // hot path: the minimum over the 32 keys, branch-free
+            // the minimum of 32 keys, computed (a tree of fminf; NaN ignored)
+            auto chunk_min = [](const uint32_t (&v)[32]) {
                 float m8[8];
 #pragma unroll
                 for (int i4 = 0; i4 < 8; ++i4)
                     m8[i4] = fminf(fminf(__uint_as_float(v[4 * i4]), __uint_as_float(v[4 * i4 + 1])),
                                    fminf(__uint_as_float(v[4 * i4 + 2]), __uint_as_float(v[4 * i4 + 3])));
-                const float mm = fminf(fminf(fminf(m8[0], m8[1]), fminf(m8[2], m8[3])),
-                                       fminf(fminf(m8[4], m8[5]), fminf(m8[6], m8[7])));
+                return fminf(fminf(fminf(m8[0], m8[1]), fminf(m8[2], m8[3])),
+                             fminf(fminf(m8[4], m8[5]), fminf(m8[6], m8[7])));
+            };
+            // examine 32 keys from columns cb.. (rem of them belong to the
+            // tile) whose minimum the load reduced to mm
+            auto examine = [&](uint32_t (&v)[32], float mm, const int2* grp, int cb, int rem) {
+                // columns past the tile's rows hold an earlier tile's values,
+                // which the load's minimum includes: NaN never passes a
+                // comparison, and the minimum is taken again without them
+                if (rem < 32) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (i >= rem) v[i] = 0x7fc00000u;
+                    mm = chunk_min(v);
+                }
                 if (!(mm <= t)) return;  // per-lane control flow only: no warp collective inside
                 if (x.timers) atomicAdd(&x.timers[TT_EPI_RARE], 1ull);
                 uint32_t m = 0;
@@ -776,48 +813,102 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                 }
             };
             int since_pub = 0;
+            uint32_t ntile = 0;  // tiles this warp has examined (diagnostics)
+            int since_flush = 0;  // tiles with buffered candidates since the last insertion
             bool dirty = false;
             for (;;) {
                 const int b = (int)acur;
                 long long te0 = (x.timers && warp == 0 && lane == 0) ? clock64() : 0;
-                const bool ok = tc::mbar_wait(&acc_full[b], ause[b] & 1u, x.spin_budget);
+                const bool ok = tc::mbar_wait(&acc_full[b], (aph >> b) & 1u, x.spin_budget);
                 if (!__all_sync(0xffffffffu, ok)) {
                     if (lane == 0) s_fail = 1;
                     break;
                 }
                 tc::fence_after_sync();
                 const int2 am = amet[b];
-                ++ause[b];
+                aph ^= 1u << b;
+                aused |= 1u << b;
                 if (NG == 1) acur ^= 1u;
                 if (am.y < 0) {  // the end of the block
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&acc_empty[b], 1);
+                    // candidates still buffered go into the lists
+                    if (__any_sync(0xffffffffu, nb > 0)) flush();
                     break;
                 }
                 long long te1 = (x.timers && warp == 0 && lane == 0) ? clock64() : 0;
                 const int nst = am.y;
-                const int2* grp = sgrp + am.x * TN8;
+                const int2* grp = sgrp + am.x * TN8;  // the tile's row-group table
                 const uint32_t tcol = tl + (uint32_t)(b * TN);
                 const int nch = (nst + 31) >> 5;
                 changed = false;
-                // a loop, not unrolled: one copy of the examine path keeps the
-                // kernel's code within the instruction cache
+                long long ld_cyc = 0;
+                // the columns 64 at a time: the load's minimum decides whether
+                // any lane needs them, and only then are they read again 32 at
+                // a time and examined (loops, not unrolled: one copy of the
+                // examine path keeps the kernel's code within the instruction
+                // cache).  A 64-column read past the tile's columns stays
+                // within the accumulator (TN is a multiple of 64); its stale
+                // columns only lower the minimum.  With two epilogue groups
+                // (registers capped lower) the columns are read 32 at a time;
+                // every 8th tile of a warp checks the load's minimum against
+                // the computed one (diagnostics).
+                if constexpr (NG == 1) {
 #pragma unroll 1
-                for (int cc = 0; cc < nch; ++cc) {
-                    uint32_t v[32];
-                    tc::tmem_ld32_wait(tcol + (uint32_t)(cc * 32), v);
-                    if (act) examine(v, grp, cc * 32, nst - cc * 32);
+                    for (int c2 = 0; c2 < nch; c2 += 2) {
+                        const long long l0 = x.timers ? clock64() : 0;
+                        const float m2 = tc::tmem_min64_wait(tcol + (uint32_t)(c2 * 32));
+                        if (x.timers) ld_cyc += clock64() - l0;
+                        const bool need = act && (nst - c2 * 32 < 64 || m2 <= t);
+                        if (!__any_sync(0xffffffffu, need)) continue;
+                        const int ce = min(c2 + 2, nch);
+#pragma unroll 1
+                        for (int cc = c2; cc < ce; ++cc) {
+                            uint32_t v[32];
+                            const float mm = tc::tmem_ld32_min_wait(tcol + (uint32_t)(cc * 32), v);
+                            if (x.timers && (ntile & 7) == 0 && act && nst - cc * 32 >= 32 && !(chunk_min(v) == mm))
+                                atomicAdd(&x.timers[TT_RED_MISMATCH], 1ull);
+                            if (act) examine(v, mm, grp, cc * 32, nst - cc * 32);
+                        }
+                    }
+                } else {
+#pragma unroll 1
+                    for (int cc = 0; cc < nch; ++cc) {
+                        uint32_t v[32];
+                        const long long l0 = x.timers ? clock64() : 0;
+                        const float mm = tc::tmem_ld32_min_wait(tcol + (uint32_t)(cc * 32), v);
+                        if (x.timers) {
+                            ld_cyc += clock64() - l0;
+                            if ((ntile & 7) == 0 && act && nst - cc * 32 >= 32 && !(chunk_min(v) == mm))
+                                atomicAdd(&x.timers[TT_RED_MISMATCH], 1ull);
+                        }
+                        if (act) examine(v, mm, grp, cc * 32, nst - cc * 32);
+                    }
                 }
+                ++ntile;
+                const long long te2 = (x.timers && warp == 0 && lane == 0) ? clock64() : 0;
                 // every lane's TMEM reads are done and its candidates' points
-                // are resolved: the accumulator and the slot go back
+                // are resolved: the accumulator and the row-group table go back
                 tc::fence_before_sync();
                 __syncwarp();
                 if (lane == 0) {
                     tc::mbar_arrive(&acc_empty[b], 1);
-                    tc::mbar_arrive(&op_empty[am.x], 1);
+                    tc::mbar_arrive(&gr_empty[am.x], 1);
                 }
-                // the whole warp inserts its buffered candidates together
-                if (__reduce_max_sync(0xffffffffu, nb) > 0) flush();
+                // the whole warp inserts its buffered candidates together, once
+                // enough lanes hold some (one pass of the insertion code then
+                // serves them all), a buffer is nearly full, or a few tiles have
+                // passed; the insertion threshold only loosens meanwhile
+                {
+                    const unsigned pend = __ballot_sync(0xffffffffu, nb > 0);
+                    if (pend) ++since_flush;
+                    if (__popc(pend) >= kFlushLanes || since_flush >= kFlushTiles ||
+                        __any_sync(0xffffffffu, nb >= CB - 2)) {
+                        flush();
+                        since_flush = 0;
+                    }
+                }
+                const long long te3 = (x.timers && warp == 0 && lane == 0) ? clock64() : 0;
                 // publish this warp's bounds for the planner's next window (a
                 // later publication only prunes later; any is valid)
                 dirty |= __any_sync(0xffffffffu, changed);
@@ -839,6 +930,9 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                 if (x.timers && warp == 0 && lane == 0) {
                     atomicAdd(&x.timers[TT_EPI_WAIT], (unsigned long long)(te1 - te0));
                     atomicAdd(&x.timers[TT_EPI_WORK], (unsigned long long)(clock64() - te1));
+                    atomicAdd(&x.timers[TT_EPI_LD], (unsigned long long)ld_cyc);
+                    atomicAdd(&x.timers[TT_EPI_LOOP], (unsigned long long)(te2 - te1));
+                    atomicAdd(&x.timers[TT_EPI_FLUSH], (unsigned long long)(te3 - te2));
                 }
             }
         }
@@ -922,7 +1016,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
         }
         if (warp == MW && lane == 0)
             for (int b = 0; b < 2; ++b)
-                if (ause[b] > 0) tc::mbar_wait(&acc_full[b], (ause[b] - 1) & 1u, kDrainPolls);
+                if ((aused >> b) & 1u) tc::mbar_wait(&acc_full[b], ((aph >> b) & 1u) ^ 1u, kDrainPolls);
         if (tid == 0) atomicExch(x.err, 1);
     }
     tc::fence_before_sync();
