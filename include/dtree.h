@@ -352,7 +352,9 @@ typedef struct dtree_train_opts {
     uint32_t seed;            /* initialisation and shuffling seed (0 = default) */
     float* loss_out;          /* optional host array: mean training loss of each epoch */
     int32_t loss_out_len;
-    int32_t reserved[8];      /* must be zero */
+    int32_t precision;        /* dtree_precision of the search that makes the labels (default
+                                 FP32); the labels are the exact neighbours at every precision */
+    int32_t reserved[7];      /* must be zero */
 } dtree_train_opts;
 
 /*

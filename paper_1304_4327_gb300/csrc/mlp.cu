@@ -665,8 +665,9 @@ int dtree_proposal_train(const dtree_t* ref, const dtree_t* train, int32_t k,
     const int seed_pts = o && o->seed_points > 0 ? o->seed_points : 512;
     if (batch > 4096 || ex_size > 1024) return DTREE_ERR_INVALID_ARG;
     if (o)
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 7; ++i)
             if (o->reserved[i]) return DTREE_ERR_INVALID_ARG;
+    if (o && (o->precision < DTREE_PREC_FP32 || o->precision > DTREE_PREC_BF16)) return DTREE_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0, major = 0, minor = 0;
     cudaGetDevice(&dev);
@@ -729,7 +730,9 @@ int dtree_proposal_train(const dtree_t* ref, const dtree_t* train, int32_t k,
     DevBuf<float> ndist;
     if ((rc = nbr.get(train->n * k, s)) != DTREE_OK) return fail(rc);
     if ((rc = ndist.get(train->n * k, s)) != DTREE_OK) return fail(rc);
-    rc = dt::knn_entry(train, ref, k, nbr.p, ndist.p, nullptr, s, nullptr, nullptr);
+    dtree_opts so{};
+    so.precision = o ? o->precision : DTREE_PREC_FP32;
+    rc = dt::knn_entry(train, ref, k, nbr.p, ndist.p, &so, s, nullptr, nullptr);
     if (rc != DTREE_OK) return fail(rc);
     // neighbour (original reference row) -> cell
     DevBuf<int32_t> cell_of;

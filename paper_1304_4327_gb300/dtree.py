@@ -47,7 +47,7 @@ class dtree_train_opts(ctypes.Structure):
     _fields_ = [("epochs", _I32), ("batch", _I32), ("lr", ctypes.c_float),
                 ("example_queries", _I32), ("seed_points", _I32), ("seed", ctypes.c_uint32),
                 ("loss_out", ctypes.POINTER(ctypes.c_float)), ("loss_out_len", _I32),
-                ("reserved", _I32 * 8)]
+                ("precision", _I32), ("reserved", _I32 * 7)]
 
 
 class DTreeError(RuntimeError):
@@ -308,13 +308,15 @@ class Model:
 
 def dtree_proposal_train(ref: Tree, train: Tree, k: int, epochs: int = 0, batch: int = 0,
                          lr: float = 0.0, example_queries: int = 0, seed_points: int = 0,
-                         seed: int = 0, stream=None) -> Model:
+                         seed: int = 0, stream=None, precision: str = "fp32") -> Model:
     """Train a leaf proposal for ``ref`` on the method's own kNN answers for the
-    points of ``train`` (see dtree.h); returns the model and its per-epoch losses."""
+    points of ``train`` (see dtree.h; ``precision`` is that search's, the answers
+    are exact at each); returns the model and its per-epoch losses."""
     n_ep = epochs if epochs > 0 else 20
     losses = (ctypes.c_float * n_ep)()
     o = dtree_train_opts(epochs=epochs, batch=batch, lr=lr, example_queries=example_queries,
-                         seed_points=seed_points, seed=seed, loss_out=losses, loss_out_len=n_ep)
+                         seed_points=seed_points, seed=seed, loss_out=losses, loss_out_len=n_ep,
+                         precision=PRECISIONS[precision])
     h = _P()
     rc = _lib.dtree_proposal_train(ref.handle, train.handle, int(k), ctypes.byref(o),
                                    _stream(stream), ctypes.byref(h))
