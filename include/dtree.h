@@ -460,9 +460,9 @@ int dtree_debug_mma(const float* A, const float* B, int32_t K, int32_t precision
  * uint64, or NULL to stop) is set, the tensor-core BaseCase pass adds
  * per-role clock64 cycle counts and event counts to counters 0..31 (window
  * preparation, slot waits and filling, MMA-issue waits, epilogue waits and
- * work, list insertions, tiles, items, TMEM reads, and chunks whose
- * load-reduced minimum differs from the computed one; the order of the
- * binding's TC_TIMERS).  Process-wide; not thread-safe.  (No counterpart in the paper:
+ * work, list insertions, tiles, items, TMEM reads, chunks whose
+ * load-reduced minimum differs from the computed one, and a bit mask of the
+ * bounded waits that gave up; the order of the binding's TC_TIMERS).  Process-wide; not thread-safe.  (No counterpart in the paper:
  * a performance probe.)
  */
 int dtree_debug_tc_timers(unsigned long long* counters);

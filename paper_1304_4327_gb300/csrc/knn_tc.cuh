@@ -279,6 +279,20 @@ struct TcExtra {
     int stall;         // diagnostics: the planner waits on a barrier nothing completes
 };
 
+// Which bounded wait gave up (diagnostics, TT_FAIL_SITES).
+enum TcFailSite {
+    FS_PLAN_SLOT = 1,   // planner: a free operand slot or row-group table
+    FS_PLAN_END = 2,    // planner: the slot for the block's end marker
+    FS_MMA_OP = 4,      // MMA warp: a filled slot
+    FS_MMA_ACC = 8,     // MMA warp: a free accumulator
+    FS_MMA_END = 16,    // MMA warp: an accumulator for the end marker
+    FS_EPI_ACC = 32,    // epilogue: a full accumulator
+    FS_STALL = 64       // the stall diagnostic
+};
+
+#define TC_FAIL_SITE(site) \
+    do { if (x.timers) atomicOr(&x.timers[TT_FAIL_SITES], (unsigned long long)(site)); } while (0)
+
 // Polls of the waits that drain a failed item's own copies and MMAs before
 // the kernel releases TMEM and exits.  They finish on their own (nothing
 // else has to run for a bulk copy or an issued MMA to complete), so the limit
@@ -311,6 +325,8 @@ enum TcTimer {
     TT_EPI_LOOP,         // epilogue (warp 0): the column loop (reads, thresholds, buffering)
     TT_EPI_FLUSH,        // epilogue (warp 0): the release and the end-of-tile insertions
     TT_MMA_WAIT_ACC,     // MMA warp: the part of TT_MMA_WAIT spent waiting for an accumulator
+    TT_FAIL_SITES,       // bit mask of the waits that gave up (TcFailSite)
+    TT_EPI_WORK_W2,      // epilogue (warp 2, alone on its sub-partition): as TT_EPI_WORK
     TT_N
 };
 static_assert(TT_N <= 32, "the diagnostic timer buffer holds 32 counters");
@@ -585,6 +601,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                                                     tc::mbar_wait(&gr_empty[gi], (guse & 1u) ^ 1u, x.spin_budget)
                                               : true;
                     if (!__all_sync(0xffffffffu, ok)) {
+                        if (lane == 0) TC_FAIL_SITE(FS_PLAN_SLOT);
                         fail = true;
                         break;
                     }
@@ -640,7 +657,10 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                 // diagnostics: a wait that nothing ends, which must give up
                 // after spin_budget polls and fail the call
                 const bool ok = lane == 0 ? tc::mbar_wait(&never, 0u, x.spin_budget) : true;
-                if (!__all_sync(0xffffffffu, ok)) fail = true;
+                if (!__all_sync(0xffffffffu, ok)) {
+                    if (lane == 0) TC_FAIL_SITE(FS_STALL);
+                    fail = true;
+                }
             }
             // the end of the block
             if (!fail) {
@@ -654,6 +674,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                     }
                     ++otile;
                 } else {
+                    if (lane == 0) TC_FAIL_SITE(FS_PLAN_END);
                     fail = true;
                 }
             }
@@ -666,6 +687,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                     const uint32_t use = otile / NB;
                     long long t0 = x.timers ? clock64() : 0;
                     if (!tc::mbar_wait(&op_full[op], use & 1u, x.spin_budget)) {
+                        TC_FAIL_SITE(FS_MMA_OP);
                         s_fail = 1;
                         break;
                     }
@@ -687,12 +709,16 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                                 acur ^= 1u;
                             }
                         }
-                        if (!ok) s_fail = 1;
+                        if (!ok) {
+                            TC_FAIL_SITE(FS_MMA_END);
+                            s_fail = 1;
+                        }
                         break;
                     }
                     const int b = (int)acur;
                     const long long ta = x.timers ? clock64() : 0;
                     if (!tc::mbar_wait(&acc_empty[b], ((aph >> b) & 1u) ^ 1u, x.spin_budget)) {
+                        TC_FAIL_SITE(FS_MMA_ACC);
                         s_fail = 1;
                         break;
                     }
@@ -821,7 +847,10 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                 long long te0 = (x.timers && warp == 0 && lane == 0) ? clock64() : 0;
                 const bool ok = tc::mbar_wait(&acc_full[b], (aph >> b) & 1u, x.spin_budget);
                 if (!__all_sync(0xffffffffu, ok)) {
-                    if (lane == 0) s_fail = 1;
+                    if (lane == 0) {
+                        TC_FAIL_SITE(FS_EPI_ACC);
+                        s_fail = 1;
+                    }
                     break;
                 }
                 tc::fence_after_sync();
@@ -836,7 +865,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                     if (__any_sync(0xffffffffu, nb > 0)) flush();
                     break;
                 }
-                long long te1 = (x.timers && warp == 0 && lane == 0) ? clock64() : 0;
+                long long te1 = (x.timers && (warp & 3) != 1 && lane == 0) ? clock64() : 0;
                 const int nst = am.y;
                 const int2* grp = sgrp + am.x * TN8;  // the tile's row-group table
                 const uint32_t tcol = tl + (uint32_t)(b * TN);
@@ -927,6 +956,8 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                     dirty = false;
                     since_pub = 0;
                 }
+                if (x.timers && warp == 2 && lane == 0)
+                    atomicAdd(&x.timers[TT_EPI_WORK_W2], (unsigned long long)(clock64() - te1));
                 if (x.timers && warp == 0 && lane == 0) {
                     atomicAdd(&x.timers[TT_EPI_WAIT], (unsigned long long)(te1 - te0));
                     atomicAdd(&x.timers[TT_EPI_WORK], (unsigned long long)(clock64() - te1));

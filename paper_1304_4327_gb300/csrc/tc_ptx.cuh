@@ -280,6 +280,7 @@ __device__ __forceinline__ float tmem_min64_wait(uint32_t taddr) {
           "=r"(r)
         : "r"(taddr)
         : "memory");
+    (void)v;
     return __uint_as_float(r);
 }
 

@@ -4,6 +4,7 @@ a barrier that nothing completes); the call must report DTREE_ERR_TIMEOUT, and
 the next call on the same context must return the oracle's lists."""
 import numpy as np
 import pytest
+import torch
 
 from paper_1304_4327_gb300 import inputs
 from parity import compare
@@ -25,13 +26,19 @@ def dt():
 def test_a_wait_that_never_ends_times_out_and_the_context_recovers(dt, prec, d, k):
     R = inputs.gaussian(20_000, d, 900 + d)
     Q = inputs.gaussian(2_000, d, 901 + d)
+    buf = torch.zeros(64, dtype=torch.int64, device="cuda")
     dt.dtree_debug_tc_stall(True)
+    dt.dtree_debug_tc_timers(buf)
     try:
         with pytest.raises(dt.DTreeError) as e:
             run(dt, R, Q, k, 32, precision=prec, spin_budget=2000)
     finally:
         dt.dtree_debug_tc_stall(False)
+        dt.dtree_debug_tc_timers(None)
     assert e.value.status == -5          # DTREE_ERR_TIMEOUT
+    # the diagnostics name the wait that gave up: the stalled one
+    sites = dict(zip(dt.TC_TIMERS, buf.cpu().tolist()))["fail_sites"]
+    assert sites & 64, sites
     idx, dist = run(dt, R, Q, k, 32, precision=prec)
     ti, td = truth(R, Q, k)
     compare(idx, dist, ti, td, k)
