@@ -327,6 +327,8 @@ enum TcTimer {
     TT_MMA_WAIT_ACC,     // MMA warp: the part of TT_MMA_WAIT spent waiting for an accumulator
     TT_FAIL_SITES,       // bit mask of the waits that gave up (TcFailSite)
     TT_EPI_WORK_W2,      // epilogue (warp 2, alone on its sub-partition): as TT_EPI_WORK
+    TT_PLAN_COPY,        // planner (lane 0's view): issuing the tile's bulk copies
+    TT_COPY_LAND,        // MMA warp: from the planner's hand-off of a slot to its wait passing
     TT_N
 };
 static_assert(TT_N <= 32, "the diagnostic timer buffer holds 32 counters");
@@ -376,6 +378,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
     float* scen = reinterpret_cast<float*>(smem + L::OFF_CEN);
     __shared__ uint64_t op_full[NB], op_empty[NB], gr_empty[GR], acc_full[2], acc_empty[2], never;
     __shared__ int ometa[NB];
+    __shared__ long long s_handoff[NB];  // diagnostics: when the planner handed each slot over
     __shared__ int2 amet[2];  // the tile in each accumulator: (table, columns), columns < 0 ends the block
     __shared__ uint32_t s_tmem;
     __shared__ int s_item;
@@ -617,10 +620,16 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                         const int gs = e.w, gg = (e.y + 7) >> 3;
                         const int lo = max(gs, g0), hi = min(gs + gg, g1);
                         int real = 0;
-                        if (valid && hi > lo) {
+                        const long long tcp = x.timers ? clock64() : 0;
+                        if (valid && hi > lo)
                             tc::bulk_g2s(slot + (lo - g0) * S::GB,
                                          rops + ((int64_t)e.z * ls8 + (lo - gs)) * S::GB,
                                          (uint32_t)(hi - lo) * S::GB, &op_full[op]);
+                        if (x.timers) {
+                            __syncwarp();
+                            if (lane == 0) atomicAdd(&x.timers[TT_PLAN_COPY], (unsigned long long)(clock64() - tcp));
+                        }
+                        if (valid && hi > lo) {
                             for (int q = lo; q < hi; ++q) {
                                 const int r0 = 8 * (q - gs);
                                 grp[q - g0] = make_int2(e.x + r0, min(8, e.y - r0));
@@ -638,6 +647,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                     if (lane == 0) ometa[op] = (g1 - g0) * 8;
                     __syncwarp();
                     if (lane == 0) {
+                        if (x.timers) s_handoff[op] = clock64();
                         tc::mbar_arrive(&op_full[op], 1);
                         if (x.timers) {
                             atomicAdd(&x.timers[TT_TILES], 1ull);
@@ -691,6 +701,8 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                         s_fail = 1;
                         break;
                     }
+                    if (x.timers && ometa[op] >= 0)
+                        atomicAdd(&x.timers[TT_COPY_LAND], (unsigned long long)(clock64() - s_handoff[op]));
                     const int nst = ometa[op];
                     ++otile;
                     if (nst < 0) {

@@ -528,7 +528,8 @@ def dtree_debug_mma(A: torch.Tensor, B: torch.Tensor, fmt: str = "bf16", stream=
 
 TC_TIMERS = ("plan_window", "plan_wait", "plan_stage", "mma_wait", "epi_wait", "epi_work",
              "epi_rare_chunks", "epi_finish", "item_setup", "tiles", "items", "inserts", "epi_ld", "red_mismatch",
-             "epi_loop", "epi_flush", "mma_wait_acc", "fail_sites", "epi_work_w2")
+             "epi_loop", "epi_flush", "mma_wait_acc", "fail_sites", "epi_work_w2",
+             "plan_copy", "copy_land")
 
 
 def dtree_debug_tc_stall(on: bool) -> None:
