@@ -63,6 +63,9 @@ def parse():
                    help="kNN workload (--op knn)")
     p.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default=None,
                    help="BaseCase arithmetic (default: the workload's)")
+    p.add_argument("--bound", choices=["box", "ball", "both"], default="box",
+                   help="Score's node lower bound d_min: boxes (kd-tree), balls (ball tree over the "
+                        "same splits) or the larger of the two")
     p.add_argument("--proposal", type=int, default=None,
                    help="learned-proposal cells per query block, 0 = none (default: the workload's)")
     p.add_argument("--train-queries", type=int, default=200_000)
@@ -397,7 +400,7 @@ def run_knn(args, rank, world, local):
                 dtree.dtree_attach_proposal(tr, model)
             _, _, st = dtree.dtree_knn(tq, tr, k, precision=prec, query_block=args.query_block,
                                        out_idx=out_idx, out_dist=out_dist, with_stats=True,
-                                       proposal=nprop)
+                                       proposal=nprop, bound=args.bound)
         finally:
             tr.free()
             tq.free()
@@ -484,7 +487,8 @@ def run_knn(args, rank, world, local):
         "dtype": "f32" if precision == "fp32" else precision,
         "data": "synthetic",
         "config": {"workload": spec["desc"], "arm": arm_name, "precision": precision,
-                   "proposal": M, "leaf_size": W.leaf_size, "query_block": args.query_block or 128,
+                   "proposal": M, "bound": args.bound, "leaf_size": W.leaf_size,
+                   "query_block": args.query_block or 128,
                    "step": "build ref tree + build query tree + dtree_knn",
                    "l2": (f"inputs ({(W.ref.nbytes + W.query.nbytes) / 1e6:.0f} MB) larger than the "
                           "129 MB L2; no flush"),

@@ -66,6 +66,20 @@ typedef enum dtree_precision {
                               2^-16) */
 } dtree_precision;
 
+/* The lower bound d_min(N_q, N_r) that Score (Algorithm 3) compares with
+ * B(N_q), and that the search's other pruning and ordering steps use for a
+ * point against a node.  The method is the same for any bound that is a true
+ * lower bound on the distance between the nodes' points (the paper's
+ * tree-independence: Section 3's space tree asks only for d_min, rho and
+ * lambda); results are identical for all three, only the pruning differs. */
+typedef enum dtree_bound {
+    DTREE_BOUND_BOX = 0,   /* the nodes' bounding hyperrectangles (a kd-tree) */
+    DTREE_BOUND_BALL = 1,  /* balls around the box centres with radius lambda, the largest
+                              distance from the centre to a point of the node (a ball tree
+                              over the same median splits): |C_q - C_r| - lambda_q - lambda_r */
+    DTREE_BOUND_BOTH = 2   /* the larger of the two (both are lower bounds) */
+} dtree_bound;
+
 /* Options; zero-initialise and set what you need (0 = default). */
 typedef struct dtree_opts {
     int32_t leaf_size;     /* dtree_build: max points per kd-tree leaf, 1..1024 (default 32) */
@@ -83,7 +97,9 @@ typedef struct dtree_opts {
                               may evaluate before the traversal, 1..17 (default 8); -1
                               skips the cap pass.  The cap only tightens bounds: results
                               are the same whatever its value */
-    int32_t reserved[9];   /* must be zero */
+    int32_t bound;         /* dtree_knn: dtree_bound of the node-pair lower bound (default
+                              DTREE_BOUND_BOX) */
+    int32_t reserved[8];   /* must be zero */
 } dtree_opts;
 
 /* Counters of one dtree_knn call (all zero if not requested). */

@@ -28,6 +28,7 @@ _SRC = os.path.join(_HERE, "dtree_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 BOUND_SOUND, BOUND_LITERAL, BOUND_B1, BOUND_NONE = 0, 1, 2, 3
+DMIN_KINDS = {"box": 0, "ball": 1, "both": 2}
 STAT_NAMES = ("scores", "prunes", "leaf_pairs", "basecases", "audit_prune",
               "audit_bound", "order", "qnodes", "incomplete")
 
@@ -51,7 +52,7 @@ def _load():
         lib = ctypes.CDLL(_LIB)
         P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
         lib.oracle_knn_brute.argtypes = [P, I64, P, I64, I32, I32, P, P, P]
-        lib.oracle_knn_dualtree.argtypes = [P, I64, P, I64, I32, I32, I32, I32, I32, I32,
+        lib.oracle_knn_dualtree.argtypes = [P, I64, P, I64, I32, I32, I32, I32, I32, I32, I32,
                                             P, P, P, P, P]
         lib.oracle_allnn_gray.argtypes = [P, I64, P, I64, I32, I32, I32, I32, P, P]
         lib.oracle_kdtree_check.argtypes = [P, I64, I32, I32, P]
@@ -112,8 +113,12 @@ def knn_brute(ref: np.ndarray, query: Optional[np.ndarray], k: int,
 
 def knn_dualtree(ref: np.ndarray, query: Optional[np.ndarray], k: int, leaf_size: int = 20,
                  bound: int = BOUND_SOUND, par_depth: int = 0,
-                 truth: Optional[Tuple[np.ndarray, np.ndarray]] = None):
+                 truth: Optional[Tuple[np.ndarray, np.ndarray]] = None, dmin: str = "box"):
     """Serial kd-tree dual-tree kNN (Algorithms 1, 2, 3 with the bound B).
+
+    ``dmin`` is Score's node lower bound: "box" (the kd-tree), "ball" (balls
+    of radius lambda around the box centres: a ball tree over the same
+    splits) or "both" (the larger).
 
     Returns (idx, d2, stats dict).  With ``truth`` = brute-force (idx, d2) the
     audit counters ``audit_prune`` (pruned pairs that held a true neighbour)
@@ -133,7 +138,8 @@ def knn_dualtree(ref: np.ndarray, query: Optional[np.ndarray], k: int, leaf_size
         ti = np.ascontiguousarray(truth[0], dtype=np.int64)
         td = np.ascontiguousarray(truth[1], dtype=np.float64)
     rc = lib.oracle_knn_dualtree(None if mono else _ptr(q), n, _ptr(r), r.shape[0], r.shape[1],
-                                 k, int(mono), leaf_size, bound, par_depth, _ptr(ti), _ptr(td),
+                                 k, int(mono), leaf_size, bound, DMIN_KINDS[dmin], par_depth,
+                                 _ptr(ti), _ptr(td),
                                  _ptr(idx), _ptr(d2), _ptr(st))
     if rc != 0:
         raise ValueError(f"oracle_knn_dualtree failed ({rc})")

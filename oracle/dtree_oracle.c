@@ -51,6 +51,12 @@
  *   R12 in Algorithm 4 the leaf-level bound is delta = max over the leaf's
  *       points of D_p (the text says delta equals B_1); the printed
  *       per-pair line "if d < delta then delta = d" is kept as a variant.
+ *   R13 Score's d_min may be any lower bound on the distance between the two
+ *       nodes' points (Section 3 asks a space tree only for d_min, rho and
+ *       lambda): the boxes' distance (the kd-tree), the distance between the
+ *       balls of radius lambda around the box centres (a ball tree over the
+ *       same splits: by R6 every point of a node lies within lambda of its
+ *       centre), or the larger of the two.
  */
 #include <math.h>
 #include <stdint.h>
@@ -69,6 +75,12 @@ enum {
     BOUND_LITERAL = 1,  /* the printed recursion of Section 5, unchanged */
     BOUND_B1 = 2,       /* B_1 alone (Gray's delta) */
     BOUND_NONE = 3      /* never prune: the plain dual-tree traversal */
+};
+
+enum {
+    DMIN_BOX = 0,   /* R13: the boxes */
+    DMIN_BALL = 1,  /* R13: the balls */
+    DMIN_BOTH = 2   /* R13: the larger of the two */
 };
 
 /* stats[] slots filled by oracle_knn_dualtree */
@@ -308,7 +320,7 @@ static double box_dmin(const otree* tq, int32_t a, const otree* tr, int32_t b) {
 
 typedef struct {
     const otree *tq, *tr;
-    int k, mono, bound_kind;
+    int k, mono, bound_kind, dmin_kind;
     int32_t stop;              /* the bound's ancestor chain ends at this node */
     double* D2;                /* nq x k, indexed by original query row */
     int64_t* N;
@@ -317,6 +329,30 @@ typedef struct {
     const double* true_maxdk;  /* audit: per query node max true D_p[k] */
     int64_t st[ST_NSTATS];
 } kctx;
+
+/* d_min between the balls around the box centres of radius lambda (R13):
+ * |C_a - C_b| - lambda_a - lambda_b, or 0 when the balls meet. */
+static double ball_dmin(const otree* tq, int32_t a, const otree* tr, int32_t b) {
+    int d = tq->d;
+    const double *lq = tq->lo + (int64_t)a * d, *hq = tq->hi + (int64_t)a * d;
+    const double *lr = tr->lo + (int64_t)b * d, *hr = tr->hi + (int64_t)b * d;
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double t = 0.5 * (lq[j] + hq[j]) - 0.5 * (lr[j] + hr[j]);
+        s += t * t;
+    }
+    double g = sqrt(s) - tq->lambda[a] - tr->lambda[b];
+    return g > 0.0 ? g : 0.0;
+}
+
+/* Score's d_min under the traversal's choice (R13). */
+static double node_dmin(const kctx* c, int32_t a, int32_t b) {
+    switch (c->dmin_kind) {
+    case DMIN_BALL: return ball_dmin(c->tq, a, c->tr, b);
+    case DMIN_BOTH: return fmax(box_dmin(c->tq, a, c->tr, b), ball_dmin(c->tq, a, c->tr, b));
+    default: return box_dmin(c->tq, a, c->tr, b);
+    }
+}
 
 static double kth(const kctx* c, int64_t q) {
     return c->N[q * c->k + c->k - 1] < 0 ? INF : sqrt(c->D2[q * c->k + c->k - 1]);
@@ -413,7 +449,7 @@ static void traverse(kctx* c, int32_t nq, int32_t nr) {
         if (nq != c->stop && tq->parent[nq] >= 0 && B > bound_of(c, tq->parent[nq]))
             c->st[ST_ORDER]++;
     }
-    double dmin = box_dmin(tq, nq, tr, nr);
+    double dmin = node_dmin(c, nq, nr);
     if (dmin > B) {                                              /* Score = inf (R3) */
         c->st[ST_PRUNES]++;
         if (c->true_idx) audit_prune(c, nq, nr);
@@ -426,7 +462,7 @@ static void traverse(kctx* c, int32_t nq, int32_t nr) {
         int32_t qc = qs[a];
         if (lr) { traverse(c, qc, nr); continue; }
         int32_t r0 = tr->left[nr], r1 = tr->right[nr];
-        if (box_dmin(tq, qc, tr, r1) < box_dmin(tq, qc, tr, r0)) {  /* closer first */
+        if (node_dmin(c, qc, r1) < node_dmin(c, qc, r0)) {        /* closer first */
             int32_t s = r0; r0 = r1; r1 = s;
         }
         traverse(c, qc, r0);
@@ -453,6 +489,7 @@ static void true_max_dk(const otree* t, int32_t n, const double* true_d2, int k,
  *   q == NULL (or mono != 0): monochromatic, the reference tree is also the
  *     query tree and a point never returns itself (R9).
  *   bound_kind: BOUND_SOUND / BOUND_LITERAL / BOUND_B1 / BOUND_NONE.
+ *   dmin_kind: DMIN_BOX / DMIN_BALL / DMIN_BOTH, Score's d_min (R13).
  *   par_depth: 0 runs Algorithm 1 once from the two roots.  p > 0 runs one
  *     independent traversal per query node at depth p (in parallel), each
  *     from that node and the reference root, and ends the bound's ancestor
@@ -465,10 +502,10 @@ static void true_max_dk(const otree* t, int32_t n, const double* true_d2, int k,
  * Output: out_idx / out_d2 (nq x k) ascending by (d2, index). */
 int oracle_knn_dualtree(const float* q, int64_t nq, const float* r, int64_t nr, int32_t d,
                         int32_t k, int32_t mono, int32_t leaf_size, int32_t bound_kind,
-                        int32_t par_depth, const int64_t* true_idx, const double* true_d2,
-                        int64_t* out_idx, double* out_d2, int64_t* stats) {
+                        int32_t dmin_kind, int32_t par_depth, const int64_t* true_idx,
+                        const double* true_d2, int64_t* out_idx, double* out_d2, int64_t* stats) {
     if (!r || !out_idx || !out_d2 || d <= 0 || k <= 0 || nr <= 0 || leaf_size < 1 ||
-        bound_kind < 0 || bound_kind > 3 || par_depth < 0)
+        bound_kind < 0 || bound_kind > 3 || dmin_kind < 0 || dmin_kind > 2 || par_depth < 0)
         return ORACLE_EINVAL;
     mono = mono || q == NULL;
     if (mono) { q = r; nq = nr; }
@@ -506,6 +543,7 @@ int oracle_knn_dualtree(const float* q, int64_t nq, const float* r, int64_t nr, 
         kctx c;
         memset(&c, 0, sizeof(c));
         c.tq = tq; c.tr = &tr; c.k = k; c.mono = mono; c.bound_kind = bound_kind;
+        c.dmin_kind = dmin_kind;
         c.stop = roots[s];
         c.D2 = out_d2; c.N = out_idx; c.B1 = B1; c.A = A; c.Blit = Bl;
         c.true_idx = true_idx; c.true_maxdk = tmax;

@@ -687,7 +687,7 @@ extern "C" int dtree_build(const float* pts, int64_t n, int32_t d, const dtree_o
     int leaf = (o && o->leaf_size) ? o->leaf_size : 32;
     if (leaf < 1 || leaf > 1024) return DTREE_ERR_INVALID_ARG;
     if (o)
-        for (int i = 0; i < 9; ++i)
+        for (int i = 0; i < 8; ++i)
             if (o->reserved[i]) return DTREE_ERR_INVALID_ARG;
     // A balanced tree with one-point leaves would leave some leaves empty
     // whenever n is not a power of two; two-point leaves never do.

@@ -160,9 +160,9 @@ extern "C" int dtree_emst(const dtree_t* t, int64_t* out_edges, float* out_dist,
     const int64_t n = t->n;
     if (n > 1 && (!out_edges || !out_dist)) return DTREE_ERR_INVALID_ARG;
     if (o) {
-        for (int i = 0; i < 9; ++i)
+        for (int i = 0; i < 8; ++i)
             if (o->reserved[i]) return DTREE_ERR_INVALID_ARG;
-        if (o->precision != DTREE_PREC_FP32) return DTREE_ERR_UNSUPPORTED;
+        if (o->precision != DTREE_PREC_FP32 || o->bound != DTREE_BOUND_BOX) return DTREE_ERR_UNSUPPORTED;
     }
     if (t->height > 30) return DTREE_ERR_UNSUPPORTED;  // the depth-first stack: one entry per lane
     int dev = 0, sms = 0;

@@ -32,9 +32,9 @@ extern "C" int dtree_kfn(const dtree_t* query, const dtree_t* ref, int32_t k, in
     if (k <= 0 || (mono ? (int64_t)k > m - 1 : (int64_t)k >= m)) return DTREE_ERR_INVALID_K;
     if (!out_idx || !out_dist || tq->d != ref->d) return DTREE_ERR_INVALID_ARG;
     if (o) {
-        for (int i = 0; i < 9; ++i)
+        for (int i = 0; i < 8; ++i)
             if (o->reserved[i]) return DTREE_ERR_INVALID_ARG;
-        if (o->precision != DTREE_PREC_FP32) return DTREE_ERR_UNSUPPORTED;
+        if (o->precision != DTREE_PREC_FP32 || o->bound != DTREE_BOUND_BOX) return DTREE_ERR_UNSUPPORTED;
     }
     // lists of up to 64 entries; the depth-first stack holds one entry per lane
     if (k > 63 || ref->height > 30) return DTREE_ERR_UNSUPPORTED;

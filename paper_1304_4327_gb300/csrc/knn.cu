@@ -96,8 +96,14 @@ __global__ void k_seed(const ProbDev* probs, const int32_t* blk_prob, int nblock
     int64_t n = 0;
     for (int L = 0; L < P.Ls; ++L) {
         int64_t l = 2 * n + 1, r = l + 1;
-        float dl = point_box_d2<DP>(c, rbox + l * 2 * DP);
-        float dr = point_box_d2<DP>(c, rbox + r * 2 * DP);
+        float dl, dr;
+        if (P.bound == DTREE_BOUND_BOX) {
+            dl = point_box_d2<DP>(c, rbox + l * 2 * DP);
+            dr = point_box_d2<DP>(c, rbox + r * 2 * DP);
+        } else {  // nearer by the search's bound (an order only: any choice is exact)
+            dl = point_dmin_down<DP>(P.bound, c, rbox + l * 2 * DP, P.rlam[l]);
+            dr = point_dmin_down<DP>(P.bound, c, rbox + r * 2 * DP, P.rlam[r]);
+        }
         n = dr < dl ? r : l;
     }
     const int span = P.hr - P.Ls;
@@ -174,6 +180,9 @@ __global__ void __launch_bounds__(256) k_expand(const ProbDev* __restrict__ prob
         const int64_t node0 = Pp->node0, qblock0 = Pp->qblock0, rleaf0 = Pp->rleaf0;
         const float* __restrict__ qbox = Pp->qbox;
         const float* __restrict__ rbox = Pp->rbox;
+        const float* __restrict__ qlam = Pp->qlam;
+        const float* __restrict__ rlam = Pp->rlam;
+        const int bound = Pp->bound;
         const int Lb = Pp->Lb, hr = Pp->hr, block0 = Pp->block0;
         const int64_t qloc = pq.x - node0;
         const int lq = level_of_node(qloc), lr = level_of_node(pq.y);
@@ -190,7 +199,10 @@ __global__ void __launch_bounds__(256) k_expand(const ProbDev* __restrict__ prob
                 const int64_t rc = cr ? 2 * (int64_t)pq.y + 1 + b : pq.y;
                 const float* qbx = qbox + qc * 2 * DP;
                 const float* rbx = rbox + rc * 2 * DP;
-                const float dmin = box_dmin_down<DP>(qbx, rbx);
+                // d_min under the search's bound: box, ball, or the larger
+                float dmin = bound != DTREE_BOUND_BALL ? box_dmin_down<DP>(qbx, rbx) : 0.f;
+                if (bound != DTREE_BOUND_BOX)
+                    dmin = fmaxf(dmin, ball_dmin_down<DP>(qbx, qlam[qc], rbx, rlam[rc]));
                 ++sc;
                 if (dmin > Bn[node0 + qc]) {  // Score() = infinity: prune every descendant pair
                     ++pr;
@@ -559,7 +571,7 @@ inline int kc_bucket(int need) {
 // problems' blocks, pairs and queries.
 template <int DP>
 int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int cap_leaves, int prec, int spin,
-                   int nprop, cudaStream_t s, dtree_stats* st, const ScratchArena* arena) {
+                   int nprop, int bound, cudaStream_t s, dtree_stats* st, const ScratchArena* arena) {
     const int64_t launches0 = g_launches.load();
     const int fmt = prec == DTREE_PREC_BF16 ? 1 : prec == DTREE_PREC_TF32 ? 2 : 0;
     // list length: k plus room for the candidates inside the error band
@@ -618,6 +630,8 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int cap
         P.rbeg = tr->nbeg;
         P.rcnt = tr->ncnt;
         P.rbox = tr->box;
+        P.rlam = tr->lam;
+        P.bound = bound;
         P.out_idx = hp[i].out_idx;
         P.out_dist = hp[i].out_dist;
         P.k = hp[i].k;
@@ -943,13 +957,15 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int cap
 
 // Shared option checks of dtree_knn and dtree_knn_batch.
 struct KnnOpts {
-    int prec, qb, seed_pts, cap, spin, nprop;
+    int prec, qb, seed_pts, cap, spin, nprop, bound;
 };
 
 int parse_opts(const dtree_opts* o, KnnOpts* ko) {
     if (o)
-        for (int i = 0; i < 9; ++i)
+        for (int i = 0; i < 8; ++i)
             if (o->reserved[i]) return DTREE_ERR_INVALID_ARG;
+    ko->bound = o ? o->bound : DTREE_BOUND_BOX;
+    if (ko->bound < DTREE_BOUND_BOX || ko->bound > DTREE_BOUND_BOTH) return DTREE_ERR_INVALID_ARG;
     ko->prec = o ? o->precision : DTREE_PREC_FP32;
     if (ko->prec < DTREE_PREC_FP32 || ko->prec > DTREE_PREC_BF16) return DTREE_ERR_INVALID_ARG;
     ko->qb = (o && o->query_block) ? o->query_block : 128;
@@ -992,11 +1008,11 @@ int run_group(int dp, const HostProb* hp, int np, const KnnOpts& ko, cudaStream_
             if (!hp[i].prop) return DTREE_ERR_NOT_TRAINED;
     }
     switch (dp) {
-        case 4: return knn_batch_impl<4>(hp, np, ko.qb, ko.seed_pts, ko.cap, ko.prec, ko.spin, ko.nprop, s, st, arena);
-        case 8: return knn_batch_impl<8>(hp, np, ko.qb, ko.seed_pts, ko.cap, ko.prec, ko.spin, ko.nprop, s, st, arena);
-        case 16: return knn_batch_impl<16>(hp, np, ko.qb, ko.seed_pts, ko.cap, ko.prec, ko.spin, ko.nprop, s, st, arena);
-        case 32: return knn_batch_impl<32>(hp, np, ko.qb, ko.seed_pts, ko.cap, ko.prec, ko.spin, ko.nprop, s, st, arena);
-        default: return knn_batch_impl<64>(hp, np, ko.qb, ko.seed_pts, ko.cap, ko.prec, ko.spin, ko.nprop, s, st, arena);
+        case 4: return knn_batch_impl<4>(hp, np, ko.qb, ko.seed_pts, ko.cap, ko.prec, ko.spin, ko.nprop, ko.bound, s, st, arena);
+        case 8: return knn_batch_impl<8>(hp, np, ko.qb, ko.seed_pts, ko.cap, ko.prec, ko.spin, ko.nprop, ko.bound, s, st, arena);
+        case 16: return knn_batch_impl<16>(hp, np, ko.qb, ko.seed_pts, ko.cap, ko.prec, ko.spin, ko.nprop, ko.bound, s, st, arena);
+        case 32: return knn_batch_impl<32>(hp, np, ko.qb, ko.seed_pts, ko.cap, ko.prec, ko.spin, ko.nprop, ko.bound, s, st, arena);
+        default: return knn_batch_impl<64>(hp, np, ko.qb, ko.seed_pts, ko.cap, ko.prec, ko.spin, ko.nprop, ko.bound, s, st, arena);
     }
 }
 

@@ -48,6 +48,7 @@ struct ProbDev {
     const int32_t* rbeg;
     const int32_t* rcnt;
     const float* rbox;  // nodes x 2 x DP; the root box's centre is the tensor-core centring point
+    const float* rlam;  // nodes: lambda (largest distance from the box centre to a point)
     const void* rops;   // tensor-core operand rows of the reference points (or null)
     int64_t rls8;       // 8-row groups per leaf in rops
     // outputs, rows in the caller's query order
@@ -67,7 +68,64 @@ struct ProbDev {
     int32_t Ls;       // level of the greedy seed subtree in the reference tree
     int32_t Lp;       // level of the learned proposal's cells (the proposed seed subtrees)
     int32_t item0;    // first work item of the problem
+    int32_t bound;    // dtree_bound of the node and point lower bounds
 };
+
+// ---- lower bounds on distances to a node (Section 3: d_min), rounded down
+// so that float32 rounding can only keep what the exact rule would prune.
+// A node's centre is its box centre 0.5 (lo + hi) (in float32 exactly as the
+// build computed lambda around it: halving is exact); lambda bounds the
+// distance from it to every point of the node.
+
+// The box-centre distance |C_a - C_b| of two nodes, rounded down.
+template <int DP>
+__device__ __forceinline__ float centre_dist_down(const float* a, const float* b) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < DP; ++j) {
+        const float t = 0.5f * (a[j] + a[DP + j]) - 0.5f * (b[j] + b[DP + j]);
+        s = fmaf(t, t, s);
+    }
+    return __fmul_rd(__fsqrt_rd(s), 1.f - rel_eps<DP>());
+}
+
+// Ball bound between two nodes: |C_a - C_b| - lambda_a - lambda_b (>= 0).
+template <int DP>
+__device__ __forceinline__ float ball_dmin_down(const float* a, float la, const float* b, float lb) {
+    return fmaxf(__fsub_rd(__fsub_rd(centre_dist_down<DP>(a, b), la), lb), 0.f);
+}
+
+// Point-to-box distance (the box's nearest point), rounded down.
+template <int DP>
+__device__ __forceinline__ float point_box_dmin_down(const float* q, const float* bx) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < DP; ++j) {
+        float g = fmaxf(fmaxf(bx[j] - q[j], q[j] - bx[DP + j]), 0.f);
+        s = fmaf(g, g, s);
+    }
+    return __fmul_rd(__fsqrt_rd(s), 1.f - rel_eps<DP>());
+}
+
+// Point-to-ball distance |q - C| - lambda (>= 0), rounded down.
+template <int DP>
+__device__ __forceinline__ float point_ball_dmin_down(const float* q, const float* bx, float lam) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < DP; ++j) {
+        const float t = q[j] - 0.5f * (bx[j] + bx[DP + j]);
+        s = fmaf(t, t, s);
+    }
+    return fmaxf(__fsub_rd(__fmul_rd(__fsqrt_rd(s), 1.f - rel_eps<DP>()), lam), 0.f);
+}
+
+// A point's lower bound against a node under the search's dtree_bound.
+template <int DP>
+__device__ __forceinline__ float point_dmin_down(int bound, const float* q, const float* bx, float lam) {
+    if (bound == DTREE_BOUND_BOX) return point_box_dmin_down<DP>(q, bx);
+    const float b = point_ball_dmin_down<DP>(q, bx, lam);
+    return bound == DTREE_BOUND_BALL ? b : fmaxf(b, point_box_dmin_down<DP>(q, bx));
+}
 
 struct TileArgs {
     const ProbDev* probs;       // the batch's problems

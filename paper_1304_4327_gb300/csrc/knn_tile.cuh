@@ -441,17 +441,6 @@ __global__ void __launch_bounds__(kQB) k_tile(const TileArgs a) {
 constexpr int kFbLeafBuf = 512;
 
 template <int DP>
-__device__ __forceinline__ float point_box_dmin_down(const float* q, const float* bx) {
-    float s = 0.f;
-#pragma unroll
-    for (int j = 0; j < DP; ++j) {
-        float g = fmaxf(fmaxf(bx[j] - q[j], q[j] - bx[DP + j]), 0.f);
-        s = fmaf(g, g, s);
-    }
-    return __fmul_rd(__fsqrt_rd(s), 1.f - rel_eps<DP>());
-}
-
-template <int DP>
 __device__ __forceinline__ float approx_d2(const float* q, const float* r) {
     const float4* r4 = reinterpret_cast<const float4*>(r);
     float f = 0.f;
@@ -521,7 +510,8 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
             } else if (!(a.csr_dmin[c0 + c - nseed] > ub)) {
                 leaf = a.csr_leaf[c0 + c - nseed];
             }
-            if (leaf >= 0 && point_box_dmin_down<DP>(q, P.rbox + (P.rleaf0 + leaf) * 2 * DP) > ub)
+            if (leaf >= 0 && point_dmin_down<DP>(P.bound, q, P.rbox + (P.rleaf0 + leaf) * 2 * DP,
+                                                 P.rlam[P.rleaf0 + leaf]) > ub)
                 leaf = -1;
         }
         if (leaf >= 0) s_lb[atomicAdd(&s_n, 1)] = leaf;
@@ -758,33 +748,60 @@ __global__ void __launch_bounds__(kQB) k_query_cap(const TileArgs a, float* qcap
             for (; lev < hr; ++lev) {
                 const int64_t l = 2 * n + 1;
                 const float* bx = P.rbox + l * 2 * DP;  // the boxes of children l and l + 1
-                float s0 = 0.f, s1 = 0.f;
+                // per child: squared distance to its box (s) and to its box
+                // centre (u, for the ball bound)
+                float s0 = 0.f, s1 = 0.f, u0 = 0.f, u1 = 0.f;
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
                     const int e = lane + 32 * t;
                     if (e < 2 * DP) {
                         const int c = e / DP, d = e % DP;
-                        const float g = fmaxf(fmaxf(bx[c * 2 * DP + d] - qd[t], qd[t] - bx[c * 2 * DP + DP + d]), 0.f);
-                        if (c == 0) s0 = fmaf(g, g, s0);
-                        else s1 = fmaf(g, g, s1);
+                        const float lo = bx[c * 2 * DP + d], hi = bx[c * 2 * DP + DP + d];
+                        const float g = fmaxf(fmaxf(lo - qd[t], qd[t] - hi), 0.f);
+                        const float w = qd[t] - 0.5f * (lo + hi);
+                        if (c == 0) {
+                            s0 = fmaf(g, g, s0);
+                            u0 = fmaf(w, w, u0);
+                        } else {
+                            s1 = fmaf(g, g, s1);
+                            u1 = fmaf(w, w, u1);
+                        }
                     }
                 }
+                const bool ball = P.bound != DTREE_BOUND_BOX;  // uniform over the warp
                 float dl, dr;
                 if (2 * DP <= 32) {
                     // child c's coordinates sit in lanes [c DP, c DP + DP)
-                    float sv = s0 + s1;
+                    float sv = s0 + s1, uv = u0 + u1;
 #pragma unroll
-                    for (int off = DP / 2; off > 0; off >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, off);
+                    for (int off = DP / 2; off > 0; off >>= 1) {
+                        sv += __shfl_xor_sync(0xffffffffu, sv, off);
+                        if (ball) uv += __shfl_xor_sync(0xffffffffu, uv, off);
+                    }
                     dl = __shfl_sync(0xffffffffu, sv, 0);
                     dr = __shfl_sync(0xffffffffu, sv, DP);
+                    u0 = __shfl_sync(0xffffffffu, uv, 0);
+                    u1 = __shfl_sync(0xffffffffu, uv, DP);
                 } else {
 #pragma unroll
                     for (int off = 16; off > 0; off >>= 1) {
                         s0 += __shfl_xor_sync(0xffffffffu, s0, off);
                         s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+                        if (ball) {
+                            u0 += __shfl_xor_sync(0xffffffffu, u0, off);
+                            u1 += __shfl_xor_sync(0xffffffffu, u1, off);
+                        }
                     }
                     dl = s0;
                     dr = s1;
+                }
+                if (ball) {
+                    // squared ball distances max(0, |q - C| - lambda)^2 (an
+                    // order and a stopping rule only: any choice is exact)
+                    const float gl = fmaxf(sqrtf(u0) - P.rlam[l], 0.f), gr = fmaxf(sqrtf(u1) - P.rlam[l + 1], 0.f);
+                    const bool both = P.bound == DTREE_BOUND_BOTH;
+                    dl = both ? fmaxf(dl, gl * gl) : gl * gl;
+                    dr = both ? fmaxf(dr, gr * gr) : gr * gr;
                 }
                 const bool right = dr < dl;
                 const float df = right ? dl : dr;

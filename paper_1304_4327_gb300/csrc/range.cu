@@ -56,9 +56,9 @@ int range_setup(const dtree_t* query, const dtree_t* ref, double d_lo, double d_
     if (tq->d != ref->d) return DTREE_ERR_INVALID_ARG;
     if (!(d_lo >= 0.0) || !(d_hi >= d_lo)) return DTREE_ERR_INVALID_ARG;  // (NaN fails both)
     if (o) {
-        for (int i = 0; i < 9; ++i)
+        for (int i = 0; i < 8; ++i)
             if (o->reserved[i]) return DTREE_ERR_INVALID_ARG;
-        if (o->precision != DTREE_PREC_FP32) return DTREE_ERR_UNSUPPORTED;
+        if (o->precision != DTREE_PREC_FP32 || o->bound != DTREE_BOUND_BOX) return DTREE_ERR_UNSUPPORTED;
     }
     if (ref->height > 30) return DTREE_ERR_UNSUPPORTED;  // the depth-first stack: one entry per lane
     int dev = 0;

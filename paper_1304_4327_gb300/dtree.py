@@ -18,13 +18,14 @@ LIB_PATH = os.path.join(_HERE, "libdtree.so")
 
 DTREE_OK = 0
 PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2}
+BOUNDS = {"box": 0, "ball": 1, "both": 2}
 _I32, _I64, _P = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
 
 
 class dtree_opts(ctypes.Structure):
     _fields_ = [("leaf_size", _I32), ("precision", _I32), ("query_block", _I32),
                 ("seed_points", _I32), ("proposal", _I32), ("spin_budget", _I32),
-                ("cap_leaves", _I32), ("reserved", _I32 * 9)]
+                ("cap_leaves", _I32), ("bound", _I32), ("reserved", _I32 * 8)]
 
 
 STAT_FIELDS = ("node_pairs_scored", "node_pairs_pruned", "leaf_pairs_emitted",
@@ -209,12 +210,13 @@ def dtree_build(points: torch.Tensor, leaf_size: int = 32, stream=None) -> Tree:
 def dtree_knn(query: Optional[Tree], ref: Tree, k: int, precision: str = "fp32",
               query_block: int = 0, seed_points: int = 0, out_idx: Optional[torch.Tensor] = None,
               out_dist: Optional[torch.Tensor] = None, stream=None, with_stats: bool = False,
-              proposal: int = 0, cap_leaves: int = 0, spin_budget: int = 0):
+              proposal: int = 0, cap_leaves: int = 0, spin_budget: int = 0, bound: str = "box"):
     """Exact kNN of every point of ``query`` (None = monochromatic) in ``ref``.
 
     Returns (idx int64 (n_q, k), dist float32 (n_q, k)) on the device, plus a
     dict of counters when ``with_stats``.  ``cap_leaves``: leaves of each
     query's cap search (0: the library's default, -1: no cap pass).
+    ``bound``: the node lower bound d_min, "box", "ball" or "both" (see dtree.h).
     """
     nq = ref.n if query is None else query.n
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -231,7 +233,7 @@ def dtree_knn(query: Optional[Tree], ref: Tree, k: int, precision: str = "fp32",
     if out_dist.shape != (nq, k) or out_dist.dtype != torch.float32 or not out_dist.is_contiguous():
         raise ValueError("out_dist must be a contiguous float32 (n_q, k) tensor")
     o = _opts(precision=PRECISIONS[precision], query_block=query_block, seed_points=seed_points,
-              proposal=proposal, cap_leaves=cap_leaves, spin_budget=spin_budget)
+              proposal=proposal, cap_leaves=cap_leaves, spin_budget=spin_budget, bound=BOUNDS[bound])
     st = dtree_stats()
     rc = _lib.dtree_knn(None if query is None else query.handle, ref.handle, int(k),
                         ctypes.c_void_p(out_idx.data_ptr()), ctypes.c_void_p(out_dist.data_ptr()),
@@ -461,7 +463,7 @@ def dtree_emst(tree: Tree, stream=None, with_stats: bool = False, precision: str
 
 def dtree_knn_noalloc(query: Optional[Tree], ref: Tree, k: int, out_idx: torch.Tensor,
                       out_dist: torch.Tensor, precision: str = "fp32", query_block: int = 0,
-                      seed_points: int = 0, stream=None, cap_leaves: int = 0) -> None:
+                      seed_points: int = 0, stream=None, cap_leaves: int = 0, bound: str = "box") -> None:
     """dtree_knn with no device allocation: the outputs are the caller's
     (contiguous int64 / float32 (n_q, k) tensors) and the library's scratch
     is a fixed static array.  Overlapping calls on one device race."""
@@ -471,7 +473,7 @@ def dtree_knn_noalloc(query: Optional[Tree], ref: Tree, k: int, out_idx: torch.T
     if out_dist.shape != (nq, k) or out_dist.dtype != torch.float32 or not out_dist.is_contiguous():
         raise ValueError("out_dist must be a contiguous float32 (n_q, k) tensor")
     o = _opts(precision=PRECISIONS[precision], query_block=query_block, seed_points=seed_points,
-              cap_leaves=cap_leaves)
+              cap_leaves=cap_leaves, bound=BOUNDS[bound])
     rc = _lib.dtree_knn_noalloc(None if query is None else query.handle, ref.handle, int(k),
                                 ctypes.c_void_p(out_idx.data_ptr()),
                                 ctypes.c_void_p(out_dist.data_ptr()), ctypes.byref(o),

@@ -292,3 +292,63 @@ def test_kdtree_structure(leaf):
     assert bad == 0
     assert nodes == 2 * leaves - 1
     assert depth >= int(np.ceil(np.log2(1000 / leaf))) - 1
+
+
+# --------------------------------------------------------------------------
+# Score's d_min as balls (a ball tree over the same splits) or as the larger
+# of boxes and balls: the traversal stays exact and prunes no true neighbour
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dmin", ["ball", "both"])
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_figure1_dualtree_ball_bounds(dmin, k):
+    P, I, D = load_figure1()
+    for leaf in (1, 2, 5):
+        idx, d2, st = oracle.knn_dualtree(P, None, k, leaf, dmin=dmin)
+        assert np.array_equal(idx, I[:, :k])
+        assert np.array_equal(d2, D[:, :k])
+
+
+@pytest.mark.parametrize("dmin", ["ball", "both"])
+@pytest.mark.parametrize("kind", sorted(DATA))
+@pytest.mark.parametrize("d", [2, 8])
+@pytest.mark.parametrize("mono", [True, False])
+def test_dualtree_ball_bounds_equal_brute(dmin, kind, d, mono):
+    R = DATA[kind](500, d, 3000 + d)
+    Q = None if mono else DATA[kind](200, d, 4000 + d)
+    for k in (1, 5):
+        truth = oracle.knn_brute(R, Q, k)
+        for leaf in (1, 8):
+            idx, d2, st = oracle.knn_dualtree(R, Q, k, leaf, truth=truth, dmin=dmin)
+            assert np.array_equal(idx, truth[0]), (k, leaf)
+            assert np.array_equal(d2, truth[1])
+            assert st["audit_prune"] == 0 and st["audit_bound"] == 0
+            assert st["incomplete"] == 0
+
+
+def test_ball_bound_prunes_separated_clusters():
+    # two clusters 100 apart: every cross pair of leaves is far beyond both
+    # balls' radii, so the ball bound alone prunes them
+    g = np.random.default_rng(7)
+    A = g.normal(0.0, 1.0, (300, 3))
+    B = g.normal(0.0, 1.0, (300, 3)) + np.array([100.0, 0.0, 0.0])
+    X = np.vstack([A, B]).astype(np.float32)
+    truth = oracle.knn_brute(X, None, 3)
+    idx, _, st = oracle.knn_dualtree(X, None, 3, 10, truth=truth, dmin="ball")
+    assert np.array_equal(idx, truth[0])
+    assert st["prunes"] > 0 and st["audit_prune"] == 0
+    assert st["basecases"] < 600 * 599 // 2
+
+
+def test_ball_bound_is_the_centre_distance_less_both_radii():
+    # one leaf per tree side: two points each, so lambda is half the pair's
+    # box diagonal and the ball distance has a closed form; a query cluster
+    # whose k-th distance is smaller than that distance is pruned against it
+    Q = np.array([[0.0, 0.0], [0.0, 1.0]], dtype=np.float32)
+    R = np.array([[0.0, 0.0], [0.0, 1.0], [10.0, 0.0], [10.0, 1.0]], dtype=np.float32)
+    # reference leaves {0, 1} and {2, 3}: centres (0, 0.5) and (10, 0.5),
+    # lambda 0.5 each; the query leaf's centre (0, 0.5), lambda 0.5:
+    # d_ball = 10 - 0.5 - 0.5 = 9 > B = 0 (k = 1, the query's own point)
+    idx, d2, st = oracle.knn_dualtree(R, Q, 1, 2, dmin="ball")
+    assert np.array_equal(idx[:, 0], [0, 1]) and np.array_equal(d2[:, 0], [0.0, 0.0])
+    assert st["prunes"] >= 1 and st["basecases"] == 4
