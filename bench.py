@@ -292,9 +292,9 @@ WORKLOADS = {
 # bytes per pair times its own pairs.  Absent where no capture of the current
 # kernel exists.
 TRAFFIC_CAPTURE = {
-    # k_tile_tc<3, 64, 64, 1>, 2M x 2M, no proposal: 7,527,982,796,544 B read +
-    # 1,676,165,376 B written over 3,823,141,564,079 point pairs
-    ("powerlaw64", "bf16"): (7_527_982_796_544 + 1_676_165_376, 3_823_141_564_079),
+    # k_tile_tc<3, 64, 64, 1>, 2M x 2M, no proposal: 7,537,166,701,312 B read +
+    # 1,357,455,360 B written over 3,823,180,810,357 point pairs
+    ("powerlaw64", "bf16"): (7_537_166_701_312 + 1_357_455_360, 3_823_180_810_357),
 }
 
 

@@ -472,14 +472,29 @@ int dtree_debug_mma(const float* A, const float* B, int32_t K, int32_t precision
                     void* stream);
 
 /*
+ * dtree_debug_tmem_min -- diagnostic: dtree_debug_mma's tile, plus the
+ * minima the BaseCase epilogue takes from the loads themselves
+ * (tcgen05.ld.red ... .min.f32): min32 (device, 128 x 4 float32) holds row
+ * i's minimum over columns [32c, 32c + 32) from a 32-column read, min64
+ * (device, 128 x 2) over [64c, 64c + 64) from a 64-column read.  Each must
+ * equal the float32 minimum of the same columns of `out`.  Status as
+ * dtree_debug_mma, and DTREE_ERR_INVALID_ARG for a null min32 or min64.
+ * (No counterpart in the paper: this checks the hardware path only.)
+ */
+int dtree_debug_tmem_min(const float* A, const float* B, int32_t K, int32_t precision, float* out,
+                         float* min32, float* min64, void* stream);
+
+/*
  * dtree_debug_tc_timers -- diagnostic: while `counters` (device, 64 zeroed
- * uint64, or NULL to stop) is set, the tensor-core BaseCase pass adds
- * per-role clock64 cycle counts and event counts to counters 0..31 (window
+ * uint64, or NULL to stop) is set, the tensor-core BaseCase pass ORs into
+ * counter TT_FAIL_SITES (the binding's TC_TIMERS order) a bit for each kind
+ * of bounded wait that gave up.  A library built with DTREE_TC_TIMERS=1
+ * also adds per-role clock64 cycle counts and event counts (window
  * preparation, slot waits and filling, MMA-issue waits, epilogue waits and
- * work, list insertions, tiles, items, TMEM reads, chunks whose
- * load-reduced minimum differs from the computed one, and a bit mask of the
- * bounded waits that gave up; the order of the binding's TC_TIMERS).  Process-wide; not thread-safe.  (No counterpart in the paper:
- * a performance probe.)
+ * work, list insertions, tiles, items, TMEM reads); the default build leaves
+ * them at zero, because their code slows the pass even when detached.
+ * Process-wide; not thread-safe.  (No counterpart in the paper: a
+ * performance probe.)
  */
 int dtree_debug_tc_timers(unsigned long long* counters);
 

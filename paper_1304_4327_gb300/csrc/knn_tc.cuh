@@ -306,7 +306,14 @@ constexpr int kFlushLanes = 8;
 constexpr int kFlushTiles = 16;
 
 // Diagnostic cycle counters of the tile kernel (summed over CTAs; read only
-// when timers are attached).
+// when timers are attached).  The per-role cycle counts are compiled in only
+// with DTREE_TC_TIMERS=1: their clock reads and registers cost the hot loops
+// about a sixth of their speed even when no counters are attached.  The
+// failure-site mask (TT_FAIL_SITES) is always kept: it sits on failure paths.
+#ifndef DTREE_TC_TIMERS
+#define DTREE_TC_TIMERS 0
+#endif
+#define TC_TIMED (DTREE_TC_TIMERS && x.timers)
 enum TcTimer {
     TT_PLAN_WINDOW = 0,  // planner: loading and preparing candidate windows
     TT_PLAN_WAIT,        // planner: waiting for a free operand slot
@@ -321,7 +328,6 @@ enum TcTimer {
     TT_ITEMS,            // items processed
     TT_INSERTS,          // epilogue (all threads): candidate-list insertions
     TT_EPI_LD,           // epilogue (warp 0): TMEM reads, issue to completion
-    TT_RED_MISMATCH,     // epilogue (all threads): load-reduced minima unlike the computed ones
     TT_EPI_LOOP,         // epilogue (warp 0): the column loop (reads, thresholds, buffering)
     TT_EPI_FLUSH,        // epilogue (warp 0): the release and the end-of-tile insertions
     TT_MMA_WAIT_ACC,     // MMA warp: the part of TT_MMA_WAIT spent waiting for an accumulator
@@ -439,7 +445,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
             __syncthreads();
             continue;
         }
-        long long tm0 = x.timers ? clock64() : 0;
+        long long tm0 = TC_TIMED ? clock64() : 0;
         // the centring point: the reference root box's centre, as k_tc_ops used it
         if (tid < DP) scen[tid] = 0.5f * (P.rbox[tid] + P.rbox[DP + tid]);
         __syncthreads();
@@ -498,7 +504,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
         }
         tc::fence_proxy_async_smem();
         __syncthreads();
-        if (x.timers && tid == 0) {
+        if (TC_TIMED && tid == 0) {
             atomicAdd(&x.timers[TT_ITEM_SETUP], (unsigned long long)(clock64() - tm0));
             atomicAdd(&x.timers[TT_ITEMS], 1ull);
         }
@@ -532,7 +538,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
             int wbuf = 0;
             for (int64_t w0 = 0; w0 < ntot && !fail; w0 += WIN, wbuf ^= 1) {
                 const int wn = (int)(ntot - w0 < WIN ? ntot - w0 : WIN);
-                long long t0 = x.timers ? clock64() : 0;
+                long long t0 = TC_TIMED ? clock64() : 0;
                 tc::cp_async_wait_all();
                 __syncwarp();
                 if (w0 + WIN < ntot) fetch(w0 + WIN, wbuf ^ 1);
@@ -589,7 +595,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                     G += __shfl_sync(0xffffffffu, incl, 31);
                 }
                 __syncwarp();
-                if (x.timers && lane == 0)
+                if (TC_TIMED && lane == 0)
                     atomicAdd(&x.timers[TT_PLAN_WINDOW], (unsigned long long)(clock64() - t0));
                 // tiles of TN8 groups; the entries overlapping a tile are consecutive
                 int cur = 0;
@@ -597,7 +603,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                     const int g1 = min(g0 + TN8, G);
                     const int op = (int)(otile % NB);
                     const uint32_t use = otile / NB;
-                    long long t1 = x.timers ? clock64() : 0;
+                    long long t1 = TC_TIMED ? clock64() : 0;
                     const int gi = (int)(gtile % GR);
                     const uint32_t guse = gtile / GR;
                     const bool ok = lane == 0 ? tc::mbar_wait(&op_empty[op], (use & 1u) ^ 1u, x.spin_budget) &&
@@ -608,7 +614,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                         fail = true;
                         break;
                     }
-                    long long t2 = x.timers ? clock64() : 0;
+                    long long t2 = TC_TIMED ? clock64() : 0;
                     if (lane == 0) tc::mbar_expect_tx(&op_full[op], (uint32_t)(g1 - g0) * S::GB);
                     __syncwarp();
                     unsigned char* slot = sB + op * TN * S::RB;
@@ -620,12 +626,12 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                         const int gs = e.w, gg = (e.y + 7) >> 3;
                         const int lo = max(gs, g0), hi = min(gs + gg, g1);
                         int real = 0;
-                        const long long tcp = x.timers ? clock64() : 0;
+                        const long long tcp = TC_TIMED ? clock64() : 0;
                         if (valid && hi > lo)
                             tc::bulk_g2s(slot + (lo - g0) * S::GB,
                                          rops + ((int64_t)e.z * ls8 + (lo - gs)) * S::GB,
                                          (uint32_t)(hi - lo) * S::GB, &op_full[op]);
-                        if (x.timers) {
+                        if (TC_TIMED) {
                             __syncwarp();
                             if (lane == 0) atomicAdd(&x.timers[TT_PLAN_COPY], (unsigned long long)(clock64() - tcp));
                         }
@@ -647,9 +653,9 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                     if (lane == 0) ometa[op] = (g1 - g0) * 8;
                     __syncwarp();
                     if (lane == 0) {
-                        if (x.timers) s_handoff[op] = clock64();
+                        if (TC_TIMED) s_handoff[op] = clock64();
                         tc::mbar_arrive(&op_full[op], 1);
-                        if (x.timers) {
+                        if (TC_TIMED) {
                             atomicAdd(&x.timers[TT_TILES], 1ull);
                             atomicAdd(&x.timers[TT_PLAN_WAIT], (unsigned long long)(t2 - t1));
                             atomicAdd(&x.timers[TT_PLAN_STAGE], (unsigned long long)(clock64() - t2));
@@ -695,13 +701,13 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                 for (;;) {
                     const int op = (int)(otile % NB);
                     const uint32_t use = otile / NB;
-                    long long t0 = x.timers ? clock64() : 0;
+                    long long t0 = TC_TIMED ? clock64() : 0;
                     if (!tc::mbar_wait(&op_full[op], use & 1u, x.spin_budget)) {
                         TC_FAIL_SITE(FS_MMA_OP);
                         s_fail = 1;
                         break;
                     }
-                    if (x.timers && ometa[op] >= 0)
+                    if (TC_TIMED && ometa[op] >= 0)
                         atomicAdd(&x.timers[TT_COPY_LAND], (unsigned long long)(clock64() - s_handoff[op]));
                     const int nst = ometa[op];
                     ++otile;
@@ -728,13 +734,13 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                         break;
                     }
                     const int b = (int)acur;
-                    const long long ta = x.timers ? clock64() : 0;
+                    const long long ta = TC_TIMED ? clock64() : 0;
                     if (!tc::mbar_wait(&acc_empty[b], ((aph >> b) & 1u) ^ 1u, x.spin_budget)) {
                         TC_FAIL_SITE(FS_MMA_ACC);
                         s_fail = 1;
                         break;
                     }
-                    if (x.timers) {
+                    if (TC_TIMED) {
                         const long long tb = clock64();
                         atomicAdd(&x.timers[TT_MMA_WAIT], (unsigned long long)(tb - t0));
                         atomicAdd(&x.timers[TT_MMA_WAIT_ACC], (unsigned long long)(tb - ta));
@@ -827,7 +833,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                     mm = chunk_min(v);
                 }
                 if (!(mm <= t)) return;  // per-lane control flow only: no warp collective inside
-                if (x.timers) atomicAdd(&x.timers[TT_EPI_RARE], 1ull);
+                if (TC_TIMED) atomicAdd(&x.timers[TT_EPI_RARE], 1ull);
                 uint32_t m = 0;
 #pragma unroll
                 for (int i = 0; i < 32; ++i) m |= (__uint_as_float(v[i]) <= t ? 1u : 0u) << i;
@@ -856,7 +862,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
             bool dirty = false;
             for (;;) {
                 const int b = (int)acur;
-                long long te0 = (x.timers && warp == 0 && lane == 0) ? clock64() : 0;
+                long long te0 = (TC_TIMED && warp == 0 && lane == 0) ? clock64() : 0;
                 const bool ok = tc::mbar_wait(&acc_full[b], (aph >> b) & 1u, x.spin_budget);
                 if (!__all_sync(0xffffffffu, ok)) {
                     if (lane == 0) {
@@ -877,7 +883,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                     if (__any_sync(0xffffffffu, nb > 0)) flush();
                     break;
                 }
-                long long te1 = (x.timers && (warp & 3) != 1 && lane == 0) ? clock64() : 0;
+                long long te1 = (TC_TIMED && (warp & 3) != 1 && lane == 0) ? clock64() : 0;
                 const int nst = am.y;
                 const int2* grp = sgrp + am.x * TN8;  // the tile's row-group table
                 const uint32_t tcol = tl + (uint32_t)(b * TN);
@@ -897,9 +903,9 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                 if constexpr (NG == 1) {
 #pragma unroll 1
                     for (int c2 = 0; c2 < nch; c2 += 2) {
-                        const long long l0 = x.timers ? clock64() : 0;
+                        const long long l0 = TC_TIMED ? clock64() : 0;
                         const float m2 = tc::tmem_min64_wait(tcol + (uint32_t)(c2 * 32));
-                        if (x.timers) ld_cyc += clock64() - l0;
+                        if (TC_TIMED) ld_cyc += clock64() - l0;
                         const bool need = act && (nst - c2 * 32 < 64 || m2 <= t);
                         if (!__any_sync(0xffffffffu, need)) continue;
                         const int ce = min(c2 + 2, nch);
@@ -907,8 +913,6 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                         for (int cc = c2; cc < ce; ++cc) {
                             uint32_t v[32];
                             const float mm = tc::tmem_ld32_min_wait(tcol + (uint32_t)(cc * 32), v);
-                            if (x.timers && (ntile & 7) == 0 && act && nst - cc * 32 >= 32 && !(chunk_min(v) == mm))
-                                atomicAdd(&x.timers[TT_RED_MISMATCH], 1ull);
                             if (act) examine(v, mm, grp, cc * 32, nst - cc * 32);
                         }
                     }
@@ -916,18 +920,14 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
 #pragma unroll 1
                     for (int cc = 0; cc < nch; ++cc) {
                         uint32_t v[32];
-                        const long long l0 = x.timers ? clock64() : 0;
+                        const long long l0 = TC_TIMED ? clock64() : 0;
                         const float mm = tc::tmem_ld32_min_wait(tcol + (uint32_t)(cc * 32), v);
-                        if (x.timers) {
-                            ld_cyc += clock64() - l0;
-                            if ((ntile & 7) == 0 && act && nst - cc * 32 >= 32 && !(chunk_min(v) == mm))
-                                atomicAdd(&x.timers[TT_RED_MISMATCH], 1ull);
-                        }
+                        if (TC_TIMED) ld_cyc += clock64() - l0;
                         if (act) examine(v, mm, grp, cc * 32, nst - cc * 32);
                     }
                 }
                 ++ntile;
-                const long long te2 = (x.timers && warp == 0 && lane == 0) ? clock64() : 0;
+                const long long te2 = (TC_TIMED && warp == 0 && lane == 0) ? clock64() : 0;
                 // every lane's TMEM reads are done and its candidates' points
                 // are resolved: the accumulator and the row-group table go back
                 tc::fence_before_sync();
@@ -949,7 +949,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                         since_flush = 0;
                     }
                 }
-                const long long te3 = (x.timers && warp == 0 && lane == 0) ? clock64() : 0;
+                const long long te3 = (TC_TIMED && warp == 0 && lane == 0) ? clock64() : 0;
                 // publish this warp's bounds for the planner's next window (a
                 // later publication only prunes later; any is valid)
                 dirty |= __any_sync(0xffffffffu, changed);
@@ -968,9 +968,9 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                     dirty = false;
                     since_pub = 0;
                 }
-                if (x.timers && warp == 2 && lane == 0)
+                if (TC_TIMED && warp == 2 && lane == 0)
                     atomicAdd(&x.timers[TT_EPI_WORK_W2], (unsigned long long)(clock64() - te1));
-                if (x.timers && warp == 0 && lane == 0) {
+                if (TC_TIMED && warp == 0 && lane == 0) {
                     atomicAdd(&x.timers[TT_EPI_WAIT], (unsigned long long)(te1 - te0));
                     atomicAdd(&x.timers[TT_EPI_WORK], (unsigned long long)(clock64() - te1));
                     atomicAdd(&x.timers[TT_EPI_LD], (unsigned long long)ld_cyc);
@@ -1009,7 +1009,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
         }
         if (epi && grp_id == 0) {
             // ---- finish the work item
-            long long tf0 = x.timers ? clock64() : 0;
+            long long tf0 = TC_TIMED ? clock64() : 0;
             const float ubk = fminf(Bd::ub(list_at(ld, kq - 1), qa), qc);
             const float band = Bd::band(ubk, qa);
             const bool ovf = act && li[KC - 1] != kEmptyIdx && !(ld[KC - 1] > band);
@@ -1044,7 +1044,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                     P.out_dist[base + j] = (float)sqrt(bd);
                 }
             }
-            if (x.timers && qt == 0)
+            if (TC_TIMED && qt == 0)
                 atomicAdd(&x.timers[TT_EPI_FINISH], (unsigned long long)(clock64() - tf0));
         }
         __syncthreads();
@@ -1070,7 +1070,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
     if (n_eval) atomicAdd(&a.stats[ST_EVALUATED], n_eval);
     if (n_pp) atomicAdd(&a.stats[ST_POINT_PAIRS], n_pp);
     if (n_re) atomicAdd(&a.stats[ST_RERANK], n_re);
-    if (x.timers && n_ins) atomicAdd(&x.timers[TT_INSERTS], n_ins);
+    if (TC_TIMED && n_ins) atomicAdd(&x.timers[TT_INSERTS], n_ins);
 }
 
 // The kernel allocates 2 TN TMEM columns; at most one CTA may be resident per

@@ -496,6 +496,7 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
         li[j] = kEmptyIdx;
     }
     const int nseed = seed_count(a.seed_nleaf, a.seed_slots, blk);
+    const int bound = P.bound;  // read once
     const int64_t c0 = a.csr_off[blk], c1 = a.csr_off[blk + 1];
     const int64_t ntot = nseed + (c1 - c0);
     if (tid == 0) s_n = 0;
@@ -510,9 +511,13 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
             } else if (!(a.csr_dmin[c0 + c - nseed] > ub)) {
                 leaf = a.csr_leaf[c0 + c - nseed];
             }
-            if (leaf >= 0 && point_dmin_down<DP>(P.bound, q, P.rbox + (P.rleaf0 + leaf) * 2 * DP,
-                                                 P.rlam[P.rleaf0 + leaf]) > ub)
-                leaf = -1;
+            if (leaf >= 0) {
+                const float* bx = P.rbox + (P.rleaf0 + leaf) * 2 * DP;
+                const float dl = bound == DTREE_BOUND_BOX
+                                     ? point_box_dmin_down<DP>(q, bx)
+                                     : point_dmin_down<DP>(bound, q, bx, P.rlam[P.rleaf0 + leaf]);
+                if (dl > ub) leaf = -1;
+            }
         }
         if (leaf >= 0) s_lb[atomicAdd(&s_n, 1)] = leaf;
         __syncthreads();

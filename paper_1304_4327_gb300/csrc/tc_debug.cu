@@ -1,5 +1,6 @@
 // tc_debug.cu -- dtree_debug_mma: one tcgen05 tile through the same operand
-// layout, descriptors and TMEM read-out as the BaseCase kernel, for tests.
+// layout, descriptors and TMEM read-out as the BaseCase kernel, for tests;
+// with it, the minima tcgen05.ld.red returns for 32 and 64 columns.
 #include <cuda_bf16.h>
 
 #include "dtree_internal.cuh"
@@ -12,7 +13,8 @@ namespace {
 
 template <int FMT, int KP>
 __global__ void __launch_bounds__(128) k_debug_mma(const float* A, const float* B, int K,
-                                                   float* out, int* err, int spin) {
+                                                   float* out, float* min32, float* min64, int* err,
+                                                   int spin) {
     constexpr int esize = FMT == 1 ? 2 : 4;
     constexpr int RB = KP * esize, NCH = RB / 16, SBO = NCH * 128;
     constexpr int NK = KP / (FMT == 1 ? 16 : 8);
@@ -84,6 +86,17 @@ __global__ void __launch_bounds__(128) k_debug_mma(const float* A, const float* 
 #pragma unroll
             for (int i = 0; i < 32; ++i) out[(warp * 32 + lane) * 128 + cc * 32 + i] = __uint_as_float(v[i]);
         }
+        if (min32) {
+            // the same accumulator read with the loads' min reduction, as the
+            // BaseCase epilogue reads it
+            const int row = warp * 32 + lane;
+            for (int cc = 0; cc < 4; ++cc) {
+                uint32_t v[32];
+                min32[row * 4 + cc] = tc::tmem_ld32_min_wait(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
+            }
+            for (int cc = 0; cc < 2; ++cc)
+                min64[row * 2 + cc] = tc::tmem_min64_wait(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 64));
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -92,20 +105,22 @@ __global__ void __launch_bounds__(128) k_debug_mma(const float* A, const float* 
 }
 
 template <int FMT, int KP>
-int run_debug(const float* A, const float* B, int K, float* out, int* err, cudaStream_t s) {
+int run_debug(const float* A, const float* B, int K, float* out, float* min32, float* min64, int* err,
+              cudaStream_t s) {
     constexpr int esize = FMT == 1 ? 2 : 4;
     size_t smem = 2 * 128 * KP * esize;
     DT_CHECK(cudaFuncSetAttribute(k_debug_mma<FMT, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
-    DT_LAUNCH((k_debug_mma<FMT, KP>), 1, 128, smem, s, A, B, K, out, err, 1 << 20);
+    DT_LAUNCH((k_debug_mma<FMT, KP>), 1, 128, smem, s, A, B, K, out, min32, min64, err, 1 << 20);
     return DTREE_OK;
 }
 
 }  // namespace
 }  // namespace dt
 
-extern "C" int dtree_debug_mma(const float* A, const float* B, int32_t K, int32_t precision,
-                               float* out, void* stream) {
+namespace {
+int debug_mma(const float* A, const float* B, int32_t K, int32_t precision, float* out, float* min32,
+              float* min64, void* stream) {
     if (!A || !B || !out || K < 1 || K > 64) return DTREE_ERR_INVALID_ARG;
     if (precision != DTREE_PREC_BF16 && precision != DTREE_PREC_TF32) return DTREE_ERR_INVALID_ARG;
     const int fmt = precision == DTREE_PREC_BF16 ? 1 : 2;  // tcgen05 operand format code
@@ -122,14 +137,14 @@ extern "C" int dtree_debug_mma(const float* A, const float* B, int32_t K, int32_
     int kp = (K + step - 1) / step * step;
     int rc = DTREE_ERR_INVALID_ARG;
     if (fmt == 1) {
-        rc = kp <= 16 ? dt::run_debug<1, 16>(A, B, K, out, err, s)
-             : kp <= 32 ? dt::run_debug<1, 32>(A, B, K, out, err, s)
-                        : dt::run_debug<1, 64>(A, B, K, out, err, s);
+        rc = kp <= 16 ? dt::run_debug<1, 16>(A, B, K, out, min32, min64, err, s)
+             : kp <= 32 ? dt::run_debug<1, 32>(A, B, K, out, min32, min64, err, s)
+                        : dt::run_debug<1, 64>(A, B, K, out, min32, min64, err, s);
     } else {
-        rc = kp <= 8 ? dt::run_debug<2, 8>(A, B, K, out, err, s)
-             : kp <= 16 ? dt::run_debug<2, 16>(A, B, K, out, err, s)
-             : kp <= 32 ? dt::run_debug<2, 32>(A, B, K, out, err, s)
-                        : dt::run_debug<2, 64>(A, B, K, out, err, s);
+        rc = kp <= 8 ? dt::run_debug<2, 8>(A, B, K, out, min32, min64, err, s)
+             : kp <= 16 ? dt::run_debug<2, 16>(A, B, K, out, min32, min64, err, s)
+             : kp <= 32 ? dt::run_debug<2, 32>(A, B, K, out, min32, min64, err, s)
+                        : dt::run_debug<2, 64>(A, B, K, out, min32, min64, err, s);
     }
     int herr = 0;
     if (rc == DTREE_OK) {
@@ -139,6 +154,18 @@ extern "C" int dtree_debug_mma(const float* A, const float* B, int32_t K, int32_
     cudaFreeAsync(err, s);
     if (rc != DTREE_OK) return rc;
     return herr ? DTREE_ERR_TIMEOUT : DTREE_OK;
+}
+}  // namespace
+
+extern "C" int dtree_debug_mma(const float* A, const float* B, int32_t K, int32_t precision,
+                               float* out, void* stream) {
+    return debug_mma(A, B, K, precision, out, nullptr, nullptr, stream);
+}
+
+extern "C" int dtree_debug_tmem_min(const float* A, const float* B, int32_t K, int32_t precision,
+                                    float* out, float* min32, float* min64, void* stream) {
+    if (!min32 || !min64) return DTREE_ERR_INVALID_ARG;
+    return debug_mma(A, B, K, precision, out, min32, min64, stream);
 }
 
 extern "C" int dtree_debug_tc_timers(unsigned long long* counters) {

@@ -81,6 +81,8 @@ def _load() -> ctypes.CDLL:
     lib.dtree_error_string.restype = ctypes.c_char_p
     lib.dtree_debug_mma.argtypes = [_P, _P, _I32, _I32, _P, _P]
     lib.dtree_debug_mma.restype = ctypes.c_int
+    lib.dtree_debug_tmem_min.argtypes = [_P, _P, _I32, _I32, _P, _P, _P, _P]
+    lib.dtree_debug_tmem_min.restype = ctypes.c_int
     lib.dtree_debug_tc_timers.argtypes = [_P]
     lib.dtree_debug_tc_timers.restype = ctypes.c_int
     lib.dtree_debug_tc_stall.argtypes = [_I32]
@@ -529,9 +531,26 @@ def dtree_debug_mma(A: torch.Tensor, B: torch.Tensor, fmt: str = "bf16", stream=
 
 
 TC_TIMERS = ("plan_window", "plan_wait", "plan_stage", "mma_wait", "epi_wait", "epi_work",
-             "epi_rare_chunks", "epi_finish", "item_setup", "tiles", "items", "inserts", "epi_ld", "red_mismatch",
+             "epi_rare_chunks", "epi_finish", "item_setup", "tiles", "items", "inserts", "epi_ld",
              "epi_loop", "epi_flush", "mma_wait_acc", "fail_sites", "epi_work_w2",
              "plan_copy", "copy_land")
+
+
+def dtree_debug_tmem_min(A: torch.Tensor, B: torch.Tensor, fmt: str = "bf16", stream=None):
+    """dtree_debug_mma's tile and the minima the tensor-core loads reduce to:
+    (tile (128, 128), min over 32 columns (128, 4), min over 64 (128, 2))."""
+    A = _check_points(A, "A")
+    B = _check_points(B, "B")
+    out = torch.empty((128, 128), dtype=torch.float32, device=A.device)
+    m32 = torch.empty((128, 4), dtype=torch.float32, device=A.device)
+    m64 = torch.empty((128, 2), dtype=torch.float32, device=A.device)
+    rc = _lib.dtree_debug_tmem_min(ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                   A.shape[1], PRECISIONS[fmt], ctypes.c_void_p(out.data_ptr()),
+                                   ctypes.c_void_p(m32.data_ptr()), ctypes.c_void_p(m64.data_ptr()),
+                                   _stream(stream))
+    if rc != DTREE_OK:
+        raise DTreeError(rc, "dtree_debug_tmem_min")
+    return out, m32, m64
 
 
 def dtree_debug_tc_stall(on: bool) -> None:

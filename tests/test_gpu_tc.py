@@ -155,30 +155,17 @@ def test_tc_powerlaw64_full_size_sampled(dt):
     assert st["fallback_queries"] < len(W.query) // 1000, st["fallback_queries"]
 
 
-@pytest.mark.parametrize("prec", ["bf16", "tf32"])
-@pytest.mark.parametrize("d", [16, 64])
-def test_tc_load_reduced_minimum(dt, prec, d):
-    """The epilogue skips 64 columns on the minimum that tcgen05.ld.red returns
-    with the load: with the diagnostic counters attached, every 8th tile also
-    computes the minimum of each 32 columns itself, and the two must agree
-    (as float32 values) on every chunk; the result stays exact."""
-    W = inputs.powerlaw64(n_ref=60_000, n_query=6_000) if d == 64 else inputs.gmm16(n_ref=60_000, n_query=6_000)
-    R = torch.from_numpy(W.ref).cuda()
-    Q = torch.from_numpy(W.query).cuda()
-    tr = dt.dtree_build(R, W.leaf_size)
-    tq = dt.dtree_build(Q, W.leaf_size)
-    buf = torch.zeros(64, dtype=torch.int64, device="cuda")
-    try:
-        dt.dtree_debug_tc_timers(buf)
-        idx, dist = dt.dtree_knn(tq, tr, W.k, precision=prec)
-        torch.cuda.synchronize()
-    finally:
-        dt.dtree_debug_tc_timers(None)
-        tr.free()
-        tq.free()
-    t = dict(zip(dt.TC_TIMERS, buf.cpu().tolist()))
-    assert t["tiles"] > 100, t
-    assert t["red_mismatch"] == 0, t
-    ti, td = truth(W.ref, W.query, W.k)
-    r = compare(idx.cpu().numpy(), dist.cpu().numpy(), ti, td, W.k)
-    assert r["exact"] + r["exempt"] == len(W.query)
+@pytest.mark.parametrize("fmt", ["bf16", "tf32"])
+@pytest.mark.parametrize("K", [8, 16, 64])
+@pytest.mark.parametrize("shift", [0.0, -3.0])
+def test_tmem_load_reduced_minimum(dt, fmt, K, shift):
+    """The epilogue skips 64 columns on the minimum that tcgen05.ld.red
+    returns with the load: on one accumulator tile (negative and positive
+    values, with shift), the 32- and 64-column minima the loads reduce to
+    equal the float32 minima of the columns read back."""
+    g = torch.Generator().manual_seed(100 + K)
+    A = torch.randn(128, K, generator=g).cuda()
+    B = (torch.randn(128, K, generator=g) + shift).cuda()
+    out, m32, m64 = dt.dtree_debug_tmem_min(A, B, fmt)
+    assert torch.equal(m32, out.view(128, 4, 32).amin(dim=2))
+    assert torch.equal(m64, out.view(128, 2, 64).amin(dim=2))
