@@ -925,10 +925,30 @@ int knn_batch_impl(const HostProb* hp, int np, int qb_cap, int seed_pts, int cap
     //    whose float32 band overflows too
     int nfb2 = 0;
     if (nfb > 0) {
+        // few such queries: each one's candidates are split over up to 64
+        // CTAs (about two per SM in all), whose lists are then merged
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaGetLastError();
+        auto slices = [&](int n) {
+            int sl = std::min(64, std::max(1, 2 * sms / n));
+            if (sl > 1) {
+                void* part = nullptr;
+                const size_t bytes = (size_t)n * sl * KC * (sizeof(double) + sizeof(int32_t));
+                if (P.get(reinterpret_cast<unsigned char**>(&part), bytes) != DTREE_OK) return 1;
+                a.fb_part = part;
+            }
+            return sl;
+        };
+        a.fb_slices = slices(nfb);
         DT_TRY(launch_query_fb<DP>(a, KC, nfb, false, s));
         DT_CHECK(cudaMemcpyAsync(&nfb2, ctr + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
         DT_CHECK(cudaStreamSynchronize(s));
-        if (nfb2 > 0) DT_TRY(launch_query_fb<DP>(a, KC, nfb2, true, s));
+        if (nfb2 > 0) {
+            a.fb_slices = slices(nfb2);
+            DT_TRY(launch_query_fb<DP>(a, KC, nfb2, true, s));
+        }
     }
     tm.mark();  // 4
     unsigned long long hs[ST_NSTAT];

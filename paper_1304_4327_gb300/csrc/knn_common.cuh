@@ -155,6 +155,11 @@ struct TileArgs {
     int* fbq_count;
     int4* fbq2_list;   // of those, queries whose float32 band overflowed too
     int* fbq2_count;
+    // the recomputation's slices per query (1: one CTA per query) and, for
+    // more, their lists: queries x slices x KC keys (float64), then as many
+    // indices
+    int fb_slices;
+    void* fb_part;
     unsigned long long* stats;
 };
 

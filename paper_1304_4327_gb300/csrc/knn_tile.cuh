@@ -457,8 +457,14 @@ __device__ __forceinline__ float approx_d2(const float* q, const float* r) {
     return f;
 }
 
+//   stage 0  one CTA per query over all of its candidate leaves (many queries)
+//   stage 1  S CTAs per query, each over 1/S of the candidates, each writing
+//            the KC best keys of its slice to part (few queries: the scan of
+//            one query's candidates then spreads over the GPU)
+//   stage 2  one CTA per query merges its S slices' lists and finishes as
+//            stage 0 does
 template <int DP, int KC, bool EXACT>
-__global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
+__global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a, int stage, int S, void* part) {
     using T = typename std::conditional<EXACT, double, float>::type;
     extern __shared__ __align__(16) unsigned char fsm[];
     T* md = reinterpret_cast<T*>(fsm);                           // KC x 128
@@ -469,7 +475,11 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
     __shared__ int s_fi[KC];
     __shared__ double s_rd[KC];
     __shared__ int s_ri[KC];
-    const int4 e = (EXACT ? a.fbq2_list : a.fbq_list)[blockIdx.x];
+    const int fq = stage == 1 ? blockIdx.x / S : blockIdx.x;  // the query's slot in its list
+    const int sl = stage == 1 ? blockIdx.x % S : 0;           // stage 1: the CTA's slice
+    T* part_d = reinterpret_cast<T*>(part);                   // [query][slice][KC]
+    int32_t* part_i = reinterpret_cast<int32_t*>(part_d + (size_t)gridDim.x * (stage == 1 ? 1 : S) * KC);
+    const int4 e = (EXACT ? a.fbq2_list : a.fbq_list)[fq];
     const int myq = e.x, blk = e.y;  // query (tree position in its problem), global block
     const ProbDev& P = a.probs[a.blk_prob[blk]];
     const int kq = P.k;  // read once: stores below could alias P
@@ -495,76 +505,114 @@ __global__ void __launch_bounds__(kQB) k_query_fb(const TileArgs a) {
         ld[j] = (T)INFINITY;
         li[j] = kEmptyIdx;
     }
-    const int nseed = seed_count(a.seed_nleaf, a.seed_slots, blk);
-    const int bound = P.bound;  // read once
-    const int64_t c0 = a.csr_off[blk], c1 = a.csr_off[blk + 1];
-    const int64_t ntot = nseed + (c1 - c0);
-    if (tid == 0) s_n = 0;
-    __syncthreads();
-    for (int64_t base = 0; base < ntot; base += kQB) {
-        // 1. test one candidate leaf per thread against the query's ball
-        const int64_t c = base + tid;
-        int leaf = -1;
-        if (c < ntot) {
-            if (c < nseed) {
-                leaf = seed_leaf(a.seed_leaf0, a.seed_nleaf, a.seed_slots, blk, (int)c);
-            } else if (!(a.csr_dmin[c0 + c - nseed] > ub)) {
-                leaf = a.csr_leaf[c0 + c - nseed];
-            }
-            if (leaf >= 0) {
-                const float* bx = P.rbox + (P.rleaf0 + leaf) * 2 * DP;
-                const float dl = bound == DTREE_BOUND_BOX
-                                     ? point_box_dmin_down<DP>(q, bx)
-                                     : point_dmin_down<DP>(bound, q, bx, P.rlam[P.rleaf0 + leaf]);
-                if (dl > ub) leaf = -1;
-            }
-        }
-        if (leaf >= 0) s_lb[atomicAdd(&s_n, 1)] = leaf;
+    if (stage != 2) {
+        const int nseed = seed_count(a.seed_nleaf, a.seed_slots, blk);
+        const int bound = P.bound;  // read once
+        const int64_t c0 = a.csr_off[blk], c1 = a.csr_off[blk + 1];
+        const int64_t ntot = nseed + (c1 - c0);
+        // this CTA's candidates: all of them, or slice sl of S
+        const int64_t c_lo = stage == 1 ? ntot * sl / S : 0, c_hi = stage == 1 ? ntot * (sl + 1) / S : ntot;
+        if (tid == 0) s_n = 0;
         __syncthreads();
-        // 2. evaluate the buffered leaves once the next round might not fit
-        const int nb = s_n;
-        const bool flush = nb > 0 && (base + kQB >= ntot || nb + kQB > kFbLeafBuf);
-        __syncthreads();  // every thread has read s_n before the next round adds to it
-        if (flush) {
-            if (tid == 0) {
-                int acc = 0;
-                for (int i = 0; i < nb; ++i) {
-                    s_pre[i] = acc;
-                    acc += P.rcnt[P.rleaf0 + s_lb[i]];
+        for (int64_t base = c_lo; base < c_hi; base += kQB) {
+            // 1. test one candidate leaf per thread against the query's ball
+            const int64_t c = base + tid;
+            int leaf = -1;
+            if (c < c_hi) {
+                if (c < nseed) {
+                    leaf = seed_leaf(a.seed_leaf0, a.seed_nleaf, a.seed_slots, blk, (int)c);
+                } else if (!(a.csr_dmin[c0 + c - nseed] > ub)) {
+                    leaf = a.csr_leaf[c0 + c - nseed];
                 }
-                s_pre[nb] = acc;
-            }
-            __syncthreads();
-            const int npts = s_pre[nb];
-            for (int p = tid; p < npts; p += kQB) {
-                int lo = 0, hi = nb - 1;  // the buffered leaf holding point p
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_pre[mid] <= p) lo = mid;
-                    else hi = mid - 1;
-                }
-                const int r = P.rbeg[P.rleaf0 + s_lb[lo]] + (p - s_pre[lo]);
-                if (mono && r == myq) continue;
-                if constexpr (EXACT) {
-                    const double d2 = exact_d2<DP>(q, P.rpts + (int64_t)r * DP);
-                    const int orig = P.ridx[r];
-                    if (key_less(d2, orig, ld[KC - 1], li[KC - 1])) list_insert(ld, li, d2, orig);
-                } else {
-                    const float d2 = approx_d2<DP>(q, P.rpts + (int64_t)r * DP);
-                    if (key_less(d2, r, ld[KC - 1], li[KC - 1])) list_insert(ld, li, d2, r);
+                if (leaf >= 0) {
+                    const float* bx = P.rbox + (P.rleaf0 + leaf) * 2 * DP;
+                    const float dl = bound == DTREE_BOUND_BOX
+                                         ? point_box_dmin_down<DP>(q, bx)
+                                         : point_dmin_down<DP>(bound, q, bx, P.rlam[P.rleaf0 + leaf]);
+                    if (dl > ub) leaf = -1;
                 }
             }
+            if (leaf >= 0) s_lb[atomicAdd(&s_n, 1)] = leaf;
             __syncthreads();
-            if (tid == 0) s_n = 0;
-            __syncthreads();
+            // 2. evaluate the buffered leaves once the next round might not fit
+            const int nb = s_n;
+            const bool flush = nb > 0 && (base + kQB >= c_hi || nb + kQB > kFbLeafBuf);
+            __syncthreads();  // every thread has read s_n before the next round adds to it
+            if (flush) {
+                if (tid == 0) {
+                    int acc = 0;
+                    for (int i = 0; i < nb; ++i) {
+                        s_pre[i] = acc;
+                        acc += P.rcnt[P.rleaf0 + s_lb[i]];
+                    }
+                    s_pre[nb] = acc;
+                }
+                __syncthreads();
+                const int npts = s_pre[nb];
+                for (int p = tid; p < npts; p += kQB) {
+                    int lo = 0, hi = nb - 1;  // the buffered leaf holding point p
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_pre[mid] <= p) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    const int r = P.rbeg[P.rleaf0 + s_lb[lo]] + (p - s_pre[lo]);
+                    if (mono && r == myq) continue;
+                    if constexpr (EXACT) {
+                        const double d2 = exact_d2<DP>(q, P.rpts + (int64_t)r * DP);
+                        const int orig = P.ridx[r];
+                        if (key_less(d2, orig, ld[KC - 1], li[KC - 1])) list_insert(ld, li, d2, orig);
+                    } else {
+                        const float d2 = approx_d2<DP>(q, P.rpts + (int64_t)r * DP);
+                        if (key_less(d2, r, ld[KC - 1], li[KC - 1])) list_insert(ld, li, d2, r);
+                    }
+                }
+                __syncthreads();
+                if (tid == 0) s_n = 0;
+                __syncthreads();
+            }
         }
     }
+    if (stage == 2) {
+        // the S slices' lists are the columns to merge (the rest are empty)
+        for (int j = 0; j < KC; ++j) {
+            md[j * kQB + tid] = tid < S ? part_d[((size_t)fq * S + tid) * KC + j] : (T)INFINITY;
+            mi[j * kQB + tid] = tid < S ? part_i[((size_t)fq * S + tid) * KC + j] : kEmptyIdx;
+        }
+    } else {
 #pragma unroll
-    for (int j = 0; j < KC; ++j) {
-        md[j * kQB + tid] = ld[j];
-        mi[j * kQB + tid] = li[j];
+        for (int j = 0; j < KC; ++j) {
+            md[j * kQB + tid] = ld[j];
+            mi[j * kQB + tid] = li[j];
+        }
     }
     __syncthreads();
+    if (stage == 1) {
+        // the slice's KC best keys (a merge of the 128 sorted thread lists)
+        if (tid == 0) {
+            int head[kQB];
+            for (int t = 0; t < kQB; ++t) head[t] = 0;
+            for (int j = 0; j < KC; ++j) {
+                int best = -1;
+                T bd = (T)INFINITY;
+                int bi = kEmptyIdx;
+                for (int t = 0; t < kQB; ++t) {
+                    if (head[t] >= KC) continue;
+                    const T d = md[head[t] * kQB + t];
+                    const int i = mi[head[t] * kQB + t];
+                    if (best < 0 || key_less(d, i, bd, bi)) {
+                        best = t;
+                        bd = d;
+                        bi = i;
+                    }
+                }
+                head[best]++;
+                part_d[(size_t)blockIdx.x * KC + j] = bd;
+                part_i[(size_t)blockIdx.x * KC + j] = bi;
+            }
+        }
+        return;
+    }
     const int64_t obase = (int64_t)P.qidx[myq] * kq;
     const int nout = EXACT ? kq : KC;
     if (tid == 0) {
@@ -642,7 +690,13 @@ int launch_query_fb(const TileArgs& a, int kc, int nfbq, bool exact, cudaStream_
         const size_t smem = (size_t)KCV * kQB * ((exact ? 8 : 4) + 4);                      \
         DT_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                       (int)smem));                                            \
-        DT_LAUNCH(kern, nfbq, kQB, smem, s, a);                                               \
+        const int S = a.fb_slices > 1 ? a.fb_slices : 1;                                       \
+        if (S > 1) {                                                                          \
+            DT_LAUNCH(kern, nfbq * S, kQB, smem, s, a, 1, S, a.fb_part);                      \
+            DT_LAUNCH(kern, nfbq, kQB, smem, s, a, 2, S, a.fb_part);                          \
+        } else {                                                                              \
+            DT_LAUNCH(kern, nfbq, kQB, smem, s, a, 0, 1, a.fb_part);                          \
+        }                                                                                     \
         return DTREE_OK;                                                                      \
     }
     switch (kc) {
