@@ -67,7 +67,9 @@ __device__ __forceinline__ float box_dmin_down(const float* a, const float* b) {
     const float4* bl = reinterpret_cast<const float4*>(b);
     const float4* bh = reinterpret_cast<const float4*>(b + DP);
     float s = 0.f;
-#pragma unroll
+    // a few float4 groups in flight per thread, not all of them: the
+    // registers of a full unroll at d = 64 would leave one CTA per SM
+#pragma unroll 4
     for (int j = 0; j < DP / 4; ++j) {
         float4 x = al[j], y = ah[j], u = bl[j], v = bh[j];
         float g0 = fmaxf(fmaxf(x.x - v.x, u.x - y.x), 0.f);
@@ -79,6 +81,32 @@ __device__ __forceinline__ float box_dmin_down(const float* a, const float* b) {
         s = fmaf(g2, g2, s);
         s = fmaf(g3, g3, s);
     }
+    return __fmul_rd(__fsqrt_rd(s), 1.f - rel_eps<DP>());
+}
+
+// The same box distance and, from the same loads, the squared distance
+// between the two box centres (the candidate order of a leaf pair).
+template <int DP>
+__device__ __forceinline__ float box_dmin_centre(const float* a, const float* b, float& o) {
+    const float4* al = reinterpret_cast<const float4*>(a);
+    const float4* ah = reinterpret_cast<const float4*>(a + DP);
+    const float4* bl = reinterpret_cast<const float4*>(b);
+    const float4* bh = reinterpret_cast<const float4*>(b + DP);
+    float s = 0.f, c = 0.f;
+#pragma unroll 4
+    for (int j = 0; j < DP / 4; ++j) {
+        const float4 x = al[j], y = ah[j], u = bl[j], v = bh[j];
+        const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+        const float us[4] = {u.x, u.y, u.z, u.w}, vs[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float g = fmaxf(fmaxf(xs[t] - vs[t], us[t] - ys[t]), 0.f);
+            s = fmaf(g, g, s);
+            const float w = 0.5f * (xs[t] + ys[t]) - 0.5f * (us[t] + vs[t]);
+            c = fmaf(w, w, c);
+        }
+    }
+    o = c;
     return __fmul_rd(__fsqrt_rd(s), 1.f - rel_eps<DP>());
 }
 
@@ -144,7 +172,7 @@ __global__ void k_seed_proposal(const ProbDev* probs, const int32_t* blk_prob, i
 constexpr int kExpandProbs = 64;
 
 template <int DP>
-__global__ void __launch_bounds__(256) k_expand(const ProbDev* __restrict__ probs,
+__global__ void __launch_bounds__(256, 2) k_expand(const ProbDev* __restrict__ probs,
                                                 const int32_t* __restrict__ node_prob,
                                                 const float* __restrict__ Bn, const int2* fin,
                                                 const int* nin, int2* fout, int* nout, int64_t cap,
@@ -199,23 +227,31 @@ __global__ void __launch_bounds__(256) k_expand(const ProbDev* __restrict__ prob
                 const int64_t rc = cr ? 2 * (int64_t)pq.y + 1 + b : pq.y;
                 const float* qbx = qbox + qc * 2 * DP;
                 const float* rbx = rbox + rc * 2 * DP;
-                // d_min under the search's bound: box, ball, or the larger
-                float dmin = bound != DTREE_BOUND_BALL ? box_dmin_down<DP>(qbx, rbx) : 0.f;
+                // d_min under the search's bound: box, ball, or the larger;
+                // for a leaf pair also the centres' squared distance (its
+                // order among the candidates), from the same box loads
+                const bool leaves = qbot && rbot;
+                float o = -1.f;
+                float dmin = bound == DTREE_BOUND_BALL ? 0.f
+                             : leaves                  ? box_dmin_centre<DP>(qbx, rbx, o)
+                                                       : box_dmin_down<DP>(qbx, rbx);
                 if (bound != DTREE_BOUND_BOX)
                     dmin = fmaxf(dmin, ball_dmin_down<DP>(qbx, qlam[qc], rbx, rlam[rc]));
                 ++sc;
                 if (dmin > Bn[node0 + qc]) {  // Score() = infinity: prune every descendant pair
                     ++pr;
-                } else if (qbot && rbot) {
+                } else if (leaves) {
                     const int blk = block0 + (int)(qc - qblock0);
                     const int leaf = (int)(rc - rleaf0);
                     if (!in_seed(sl0, sn, slots, blk, leaf)) {  // else evaluated by the seed
                         // evaluation order: squared distance between the box centres
-                        float o = 0.f;
+                        if (o < 0.f) {
+                            o = 0.f;
 #pragma unroll
-                        for (int j = 0; j < DP; ++j) {
-                            float t = 0.5f * (qbx[j] + qbx[DP + j]) - 0.5f * (rbx[j] + rbx[DP + j]);
-                            o = fmaf(t, t, o);
+                            for (int j = 0; j < DP; ++j) {
+                                float t = 0.5f * (qbx[j] + qbx[DP + j]) - 0.5f * (rbx[j] + rbx[DP + j]);
+                                o = fmaf(t, t, o);
+                            }
                         }
                         e4 = make_int4(blk, leaf, __float_as_int(dmin), __float_as_int(o));
                         do_emit = true;
