@@ -300,10 +300,14 @@ enum TcFailSite {
 // spin_budget.
 constexpr int kDrainPolls = 1 << 22;
 // End-of-tile insertion policy of the tile kernel's epilogue warps: insert
-// when at least kFlushLanes lanes hold buffered candidates, or after
-// kFlushTiles tiles with some pending.
-constexpr int kFlushLanes = 8;
-constexpr int kFlushTiles = 16;
+// when at least flush_lanes(KC) lanes hold buffered candidates, or after
+// flush_tiles(KC) tiles with some pending.  A pass of the insertion code
+// costs in proportion to the list length, so long lists wait for more lanes
+// (2M x 2M, d = 64, lists of 64: 1.84 -> 1.79 s), while short ones insert
+// early and keep their threshold tight (gmm16, lists of 24: 32 lanes would
+// cost 5%).
+__host__ __device__ constexpr int flush_lanes(int kc) { return kc >= 48 ? 32 : 8; }
+__host__ __device__ constexpr int flush_tiles(int kc) { return kc >= 48 ? 64 : 16; }
 
 // Diagnostic cycle counters of the tile kernel (summed over CTAs; read only
 // when timers are attached).  The per-role cycle counts are compiled in only
@@ -943,7 +947,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1) k_tile_tc(const TileArgs
                 {
                     const unsigned pend = __ballot_sync(0xffffffffu, nb > 0);
                     if (pend) ++since_flush;
-                    if (__popc(pend) >= kFlushLanes || since_flush >= kFlushTiles ||
+                    if (__popc(pend) >= flush_lanes(KC) || since_flush >= flush_tiles(KC) ||
                         __any_sync(0xffffffffu, nb >= CB - 2)) {
                         flush();
                         since_flush = 0;
