@@ -181,8 +181,13 @@ __global__ void __launch_bounds__(256, 2) k_expand(const ProbDev* __restrict__ p
                                                 int* overflow, unsigned long long* stats, int np) {
     // the first kExpandProbs problems' descriptors are staged in shared memory
     extern __shared__ ProbDev sprob[];
+    __shared__ int s_stop;
+    // a fixed-range traversal whose pair storage already overflowed (an
+    // earlier level) expands no further: its call returns DTREE_ERR_TOO_LARGE
+    if (threadIdx.x == 0) s_stop = *reinterpret_cast<volatile int*>(overflow);
     for (int p = threadIdx.x; p < min(np, kExpandProbs); p += blockDim.x) sprob[p] = probs[p];
     __syncthreads();
+    if (s_stop) return;  // uniform over the CTA
     const int n = (int)min((int64_t)*nin, cap);  // the counter runs past cap on overflow
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
