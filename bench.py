@@ -543,7 +543,7 @@ def run_batched(args, rank, world, local):
     import torch.distributed as dist
     from paper_1304_4327_gb300 import autotune
 
-    precision = args.precision or "fp32"
+    precision = args.precision or "bf16"
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -582,16 +582,25 @@ def run_batched(args, rank, world, local):
                 tr.free()
         return outs, st
 
+    # the batch's inputs (80 MB) fit the 129 MB L2: before every timed step a
+    # 256 MB buffer is written, outside the step's events, so no step finds
+    # the previous one's data in L2
+    l2_flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
     def timed(n, batched=True):
         barrier()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        res = [step(pts, batched) for _ in range(n)]
-        e1.record(stream)
-        torch.cuda.synchronize()
+        total, res = 0.0, []
+        for _ in range(n):
+            l2_flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res.append(step(pts, batched))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
         barrier()
-        return max_over_ranks(e0.elapsed_time(e1) / n, world, "cuda"), res
+        return max_over_ranks(total / n, world, "cuda"), res
 
     for _ in range(args.warmup):
         step(pts)
@@ -662,7 +671,7 @@ def run_batched(args, rank, world, local):
         "data": "synthetic",
         "config": {"workload": WORKLOAD_BATCHED, "precision": precision,
                    "step": "build 256 trees + one dtree_knn_batch",
-                   "l2": "inputs (80 MB) and trees below the 129 MB L2 share; each step rebuilds them",
+                   "l2": "inputs (80 MB) fit the 129 MB L2: a 256 MB buffer is written before each timed step, outside its events",
                    "parallelism": f"{world} GPU(s), every rank its own copy of the batch",
                    "autotune_s": tune_s, "classes": len(tuner.table)},
         "roofline": roof,
@@ -963,15 +972,22 @@ def run_emst(args, rank, world, local):
     torch.cuda.synchronize()
     clocks.start()
     launches0 = dtree.launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    stats = [step(p_d) for _ in range(args.steps)]
-    e1.record(stream)
-    torch.cuda.synchronize()
+    # the points (12 MB) fit the 129 MB L2: before every timed step a 256 MB
+    # buffer is written, outside the step's events
+    l2_flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    total, stats = 0.0, []
+    for _ in range(args.steps):
+        l2_flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats.append(step(p_d))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
     barrier()
     clock_info = clocks.stop()
     launches = dtree.launch_count() - launches0
-    ms_max = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
+    ms_max = max_over_ranks(total / args.steps, world, "cuda")
     value = job_rate(world, n, ms_max)
     p_h = torch.from_numpy(P).pin_memory()
     p_e = torch.empty_like(p_d)
@@ -994,7 +1010,7 @@ def run_emst(args, rank, world, local):
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload, "step": "build tree + dtree_emst (Boruvka rounds)",
-                   "l2": "inputs (12 MB) fit L2; every step rebuilds the tree",
+                   "l2": "inputs (12 MB) fit the 129 MB L2: a 256 MB buffer is written before each timed step, outside its events",
                    "parallelism": f"{world} GPU(s), one problem each"},
         "roofline": {"bound": "fp64", "kernel": "k_emst_nn (one warp per point, float64 distances)",
                      "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
