@@ -84,8 +84,10 @@ typedef enum dtree_bound {
 typedef struct dtree_opts {
     int32_t leaf_size;     /* dtree_build: max points per kd-tree leaf, 1..1024 (default 32) */
     int32_t precision;     /* dtree_knn: dtree_precision (default FP32) */
-    int32_t query_block;   /* dtree_knn: max queries per work unit (query-tree node), 16..128
-                              (default 128) */
+    int32_t query_block;   /* dtree_knn: max queries per query block (the query-tree node that
+                              is the traversal's unit), 16..512 (default 128); a block of
+                              more than 128 queries is processed as chunks of 128 that
+                              share its candidate leaves */
     int32_t seed_points;   /* dtree_knn: min reference points of the seed subtree evaluated
                               before the traversal (default 64) */
     int32_t proposal;      /* dtree_knn: M > 0 evaluates each query block's top-M cells of the
@@ -275,7 +277,7 @@ typedef struct dtree_problem {
     const dtree_t* query;   /* NULL (or == ref): monochromatic */
     const dtree_t* ref;
     int32_t k;
-    int32_t query_block;    /* queries per block of this problem, 16..128, or 0 for
+    int32_t query_block;    /* queries per block of this problem, 16..512, or 0 for
                                opts->query_block */
     int64_t* out_idx;       /* device, n_q x k */
     float* out_dist;        /* device, n_q x k */

@@ -17,7 +17,7 @@ import os
 from typing import Dict, Iterable, List, Optional, Sequence, Tuple
 
 LEAVES = (8, 16, 32, 64)
-BLOCKS = (32, 64, 128)
+BLOCKS = (32, 64, 128, 256, 512)
 
 
 def width_bucket(d: int) -> int:

@@ -1030,7 +1030,7 @@ int parse_opts(const dtree_opts* o, KnnOpts* ko) {
     ko->prec = o ? o->precision : DTREE_PREC_FP32;
     if (ko->prec < DTREE_PREC_FP32 || ko->prec > DTREE_PREC_BF16) return DTREE_ERR_INVALID_ARG;
     ko->qb = (o && o->query_block) ? o->query_block : 128;
-    if (ko->qb < 16 || ko->qb > 128) return DTREE_ERR_INVALID_ARG;
+    if (ko->qb < 16 || ko->qb > 512) return DTREE_ERR_INVALID_ARG;
     ko->nprop = o ? o->proposal : 0;
     if (ko->nprop < 0 || ko->nprop > 8) return DTREE_ERR_INVALID_ARG;
     ko->seed_pts = (o && o->seed_points > 0) ? o->seed_points : 64;
@@ -1136,7 +1136,7 @@ extern "C" int dtree_knn_batch(int32_t nprob, const dtree_problem* probs, const 
     std::vector<dt::HostProb> hp(nprob);
     for (int i = 0; i < nprob; ++i) {
         const int qb = probs[i].query_block;
-        if (qb != 0 && (qb < 16 || qb > 128)) return DTREE_ERR_INVALID_ARG;
+        if (qb != 0 && (qb < 16 || qb > 512)) return DTREE_ERR_INVALID_ARG;
         rc = dt::check_problem(probs[i].query, probs[i].ref, probs[i].k, probs[i].out_idx,
                                probs[i].out_dist, &hp[i]);
         if (rc != DTREE_OK) return rc;
