@@ -299,9 +299,10 @@ WORKLOADS = {
 # bytes per pair times its own pairs.  Absent where no capture of the current
 # kernel exists.
 TRAFFIC_CAPTURE = {
-    # k_tile_tc<3, 64, 64, 1>, 2M x 2M, no proposal: 7,117,029,545,728 B read +
-    # 1,355,147,776 B written over 3,822,927,098,868 point pairs
-    ("powerlaw64", "bf16"): (7_117_029_545_728 + 1_355_147_776, 3_822_927_098_868),
+    # k_tile_tc<3, 64, 64, 1>, 2M x 2M, 512-query blocks, no proposal:
+    # 6,941,407,034,112 B read + 1,359,624,448 B written over
+    # 3,867,716,373,340 point pairs
+    ("powerlaw64", "bf16"): (6_941_407_034_112 + 1_359_624_448, 3_867_716_373_340),
 }
 
 
