@@ -185,3 +185,27 @@ def test_proposal_with_tensor_cores_at_k50_d64(dt):
     finally:
         for t in (tr, tq, tt):
             t.free()
+
+
+def test_the_combined_configuration_at_small_size(dt):
+    """The headline's combination at 60k x 6k: labels from a BF16 search, the
+    proposal (M = 1) with BF16 tiles and 512-query blocks; the lists equal the
+    plain FP32 search's with 128-query blocks and the oracle's."""
+    W = inputs.powerlaw64(n_ref=60_000, n_query=6_000, n_train=6_000)
+    tr = dt.dtree_build(torch.from_numpy(W.ref).cuda(), W.leaf_size)
+    tq = dt.dtree_build(torch.from_numpy(W.query).cuda(), W.leaf_size)
+    tt = dt.dtree_build(torch.from_numpy(W.extra["train"]).cuda(), W.leaf_size)
+    try:
+        model = dt.dtree_proposal_train(tr, tt, W.k, epochs=5, batch=64, precision="bf16")
+        dt.dtree_attach_proposal(tr, model)
+        plain = dt.dtree_knn(tq, tr, W.k, precision="fp32", query_block=128)
+        idx, dist = dt.dtree_knn(tq, tr, W.k, precision="bf16", proposal=1, query_block=512)
+        ti, td = truth(W.ref, W.query, W.k)
+        r = compare(idx.cpu().numpy(), dist.cpu().numpy(), ti, td, W.k)
+        assert r["exact"] + r["exempt"] == len(W.query)
+        assert torch.equal(idx, plain[0])
+        dt.dtree_attach_proposal(tr, None)
+        model.free()
+    finally:
+        for t in (tr, tq, tt):
+            t.free()
