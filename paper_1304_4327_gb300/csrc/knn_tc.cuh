@@ -1,7 +1,8 @@
 // knn_tc.cuh -- the kNN BaseCase (Algorithm 2) on the tensor cores.
 //
-// A work item is a query block of <= 128 queries (one TMEM lane and one
-// epilogue thread each).  Every point is centred on one point c, the centre
+// A work item is a chunk of <= 128 queries of a query block (one TMEM lane
+// and one epilogue thread each); the chunks of a block share its candidate
+// leaves.  Every point is centred on one point c, the centre
 // of the reference tree's root box, and rounded to the MMA's input type:
 //   - reference points once per tree and format (k_tc_ops), into an operand
 //     array laid out exactly as the tiles sit in shared memory (8-row groups
@@ -363,7 +364,7 @@ static_assert(TT_N <= 32, "the diagnostic timer buffer holds 32 counters");
 //              accumulator (two in turn) with tcgen05.mma
 // Hand-over by mbarriers: op_full (planner -> MMA: its arrival plus the
 // copied bytes), acc_full (MMA -> epilogue: the MMA's commit plus the
-// issuer's arrival with the tile's slot and columns), acc_empty (epilogue ->
+// issuer's arrival with the tile's row-group table and columns), acc_empty (epilogue ->
 // MMA: one arrival per warp once its lanes are read), op_empty (MMA commit
 // -> planner), gr_empty (the four epilogue warps -> planner: the tile's
 // row-group table is read).  Every wait is bounded; after a
