@@ -269,6 +269,9 @@ WORKLOADS = {
         # leaves): at d = 64 the bound prunes almost nothing, and the
         # traversal over 4x fewer blocks takes 94 ms instead of 344
         "query_block": 512,
+        # a per-query cap search of 16 leaves (the library's default is 8):
+        # its 41 ms more buy 63 ms of the main pass
+        "cap_leaves": 16,
     },
     # the learned-proposal configuration at d = 8.  FP32 tiles: at this point
     # density the k-th neighbour's squared distance (~1e-5) is no larger than
@@ -409,7 +412,8 @@ def run_knn(args, rank, world, local):
                 dtree.dtree_attach_proposal(tr, model)
             _, _, st = dtree.dtree_knn(tq, tr, k, precision=prec, query_block=qblock,
                                        out_idx=out_idx, out_dist=out_dist, with_stats=True,
-                                       proposal=nprop, bound=args.bound)
+                                       proposal=nprop, bound=args.bound,
+                                       cap_leaves=spec.get("cap_leaves", 0))
         finally:
             tr.free()
             tq.free()
@@ -502,7 +506,7 @@ def run_knn(args, rank, world, local):
         "data": "synthetic",
         "config": {"workload": spec["desc"], "arm": arm_name, "precision": precision,
                    "proposal": M, "bound": args.bound, "leaf_size": W.leaf_size,
-                   "query_block": qblock,
+                   "query_block": qblock, "cap_leaves": spec.get("cap_leaves", 8),
                    "step": "build ref tree + build query tree + dtree_knn",
                    "l2": (f"inputs ({(W.ref.nbytes + W.query.nbytes) / 1e6:.0f} MB) larger than the "
                           "129 MB L2; no flush"),
