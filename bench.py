@@ -334,7 +334,7 @@ def roofline(precision, d, pairs, ns_tile, sms, traffic):
         bf16 = float(peaks.get("bf16_tflops_sustained", 1700.0))
         peak = bf16 if precision == "bf16" else bf16 * 1.1 / 2.25
         bound, kernel = "tensor", f"k_tile_tc main launch (BaseCase, tcgen05 {precision})"
-        psrc = (f"measured sustained BF16 dense {bf16:.1f} TFLOP/s ({src})"
+        psrc = (f"sustained BF16 dense {bf16:.1f} TFLOP/s ({src})"
                 + ("" if precision == "bf16" else " x 1.1/2.25 (nominal TF32:BF16)"))
     achieved = flops / secs / 1e12 if secs > 0 else 0.0
     return {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak,
